@@ -1,0 +1,398 @@
+"""Stem-contraction benchmark: stem TFLOP/s and slices/s on one GB300.
+
+Workload (default): 53-qubit diagonal-lattice stand-in for Sycamore, 14
+cycles, 6 open qubits (64-amplitude batch), contraction width <= 30 (stem
+tensors up to 2^30 complex64 = 8 GiB), seeded synthetic circuit. A step is
+one batch of slices through the whole stem (every fused pass / GEMM step, the
+FP64 slice sum). Stem FLOPs follow the paper's convention: 8 real flops per
+unit of contraction cost (Table 1 arithmetic), over the stem steps of each
+slice.
+
+Also measured in the same run: the plain FP32 path (per step a permute then a
+SIMT GEMM, one slice per launch), per-launch CUDA-event timings of one batch
+(roofline of the dominant kernel), the same call with host buffers (e2e), SM
+clocks during the timed region, and the FP64 CPU oracle on a bounded sample
+of the same workload.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+                    [--impl reference]
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from synthetic.circuits import CONFIGS, config_circuit, random_bits  # noqa: E402
+
+DEFAULT_WORKLOAD = "diag53_m14"
+METRIC = "stem TFLOP/s and slices/s at 53q/14-cycle, chosen vs plain FP32 at <=1e-5 rel err"
+
+
+def plan_options(name: str) -> dict:
+    """Planner options of each workload (shared by the bench and its tests)."""
+    cfg = CONFIGS[name]
+    o = dict(cw_limit=cfg.get("cw_limit") or 30, restarts=8, local_opt_iters=4, seed=0x5EED)
+    if cfg.get("n_sliced"):
+        o["min_sliced"] = cfg["n_sliced"]
+    return o
+
+
+def workload_inputs(name: str):
+    cfg = CONFIGS[name]
+    c = config_circuit(name)
+    oq = c.layout.open_qubits(cfg["n_open"])
+    cb = list(random_bits(c.n_qubits - len(oq), cfg["bit_seed"]))
+    return c, oq, cb
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except Exception:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except Exception:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        pw = [num(r[3]) for r in rows if num(r[3]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        load = [s for s in sm if mx and s > 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(load) if load else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------- CPU oracle
+
+def oracle_sample(name: str, budget_s: float, order=None, sliced_wires=None, plan_info=None):
+    """Time the FP64 oracle on a bounded sample of the workload: the pairwise
+    contractions of slice 0 along the plan's order, in order, until the time
+    budget is spent. Returns (stem-tc done, seconds, steps done)."""
+    import oracle
+    c, oq, cb = workload_inputs(name)
+    net = oracle.build_network(c, oq, cb)
+    if sliced_wires:
+        net = oracle.fix_edges(net, oracle.slice_assignment(sliced_wires, 0))
+    live = {i: (T, list(el)) for i, (T, el) in enumerate(zip(net.tensors, net.edges))}
+    N = len(net.tensors)
+    tc = 0.0
+    done = 0
+    t0 = time.perf_counter()
+    for k, (a, b) in enumerate(order):
+        A, ea = live.pop(int(a))
+        B, eb = live.pop(int(b))
+        eab = len(set(ea) | set(eb))
+        Cm, ec = oracle.contract_pair(A, ea, B, eb)
+        live[N + k] = (Cm, ec)
+        tc += 2.0 ** eab
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    return tc, time.perf_counter() - t0, done
+
+
+def oracle_threads() -> int:
+    v = os.environ.get("OMP_NUM_THREADS")
+    return int(v) if v else (os.cpu_count() or 1)
+
+
+# ----------------------------------------------------------------- main
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(path)), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def run_reference(args):
+    """The oracle arm: FP64 CPU contraction of bounded samples of the same
+    workload (each step one bounded sample), same metric and units."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    name = args.workload
+    cfg_plan = _host_plan(name)
+    order, wires, info = cfg_plan
+    steps = []
+    budget = max(2.0, args.ref_budget / max(1, args.steps + args.warmup))
+    for i in range(args.warmup + args.steps):
+        tc, secs, done = oracle_sample(name, budget, order, wires, info)
+        if i >= args.warmup:
+            steps.append((tc, secs, done))
+    tc = sum(s[0] for s in steps)
+    secs = sum(s[1] for s in steps)
+    tflops = 8.0 * tc / secs / 1e12
+    slices = tc / info["stem_tc_per_slice"] / secs
+    line = {"impl": "reference", "metric": METRIC, "value": tflops, "unit": "TFLOP/s",
+            "slices_per_s": slices, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * secs / max(1, len(steps)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": name, "n_qubits": 53, "cycles": CONFIGS[name]["cycles"],
+                       "n_open": CONFIGS[name]["n_open"], "cw": info["cw"]},
+            "cpu_baseline": {"value": tflops, "unit": "TFLOP/s", "cores": oracle_threads(),
+                             "kind": "oracle",
+                             "sample": f"pairwise FP64 contractions of slice 0 along the plan's "
+                                       f"order, {budget:.0f} s per step"},
+            "e2e": {"value": tflops, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _host_plan(name):
+    import paper_2005_06787_gb300 as P
+    c, oq, cb = workload_inputs(name)
+    net = P.tn_build_network(c, oq, cb)
+    plan = P.tn_plan_create(net, **plan_options(name))
+    order, sl = P.tn_plan_export(plan)
+    _, _, q, s = net.info()
+    wires = [(int(q[e]), int(s[e])) for e in sl]
+    return order, wires, P.tn_plan_info(plan)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(CONFIGS))
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--plain-steps", type=int, default=2)
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--ref-budget", type=float, default=60.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    sys.path.insert(0, ROOT)
+    from paper_2005_06787_gb300._build import build as build_lib
+    build_lib()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import paper_2005_06787_gb300 as P
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.current_stream()
+    name = args.workload
+    c, oq, cb = workload_inputs(name)
+    net = P.tn_build_network(c, oq, cb)
+    t0 = time.perf_counter()
+    plan = P.tn_plan_create(net, **plan_options(name))
+    plan_s = time.perf_counter() - t0
+    P.tn_plan_prepare(plan, stream=stream)
+    torch.cuda.synchronize()
+    info = P.tn_plan_info(plan)
+    SB = info["batch_items"] // max(info["n_prefixes"], 1)
+    n_slices_total = 1 << info["n_sliced"]
+    nb = max(info["n_prefixes"], 1) << info["n_open"]
+    out = torch.zeros(2 * nb, dtype=torch.float64, device="cuda")
+    flops_per_slice = 8.0 * info["stem_tc_per_slice"]
+
+    # this rank's slice range: disjoint per rank (weak scaling)
+    per_rank = (args.warmup + args.steps) * SB
+    base = (rank * per_rank) % max(1, n_slices_total - per_rank + 1)
+
+    def step(i, mode="fused", sb=SB, host_out=None):
+        s0 = base + i * sb
+        P.tn_contract_stem(plan, s0, s0 + sb, out if host_out is None else host_out,
+                           prec="fp32", mode=mode, stream=stream, accumulate=(i > 0))
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev) as clk:
+        e0.record(stream)
+        for i in range(args.steps):
+            step(args.warmup + i)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    clocks = clk.summary()
+    slices_done = args.steps * SB * world
+    slices_per_s = slices_done / (ms / 1e3)
+    tflops = slices_per_s * flops_per_slice / 1e12
+    amps = out.cpu().numpy().view(np.complex128)
+
+    # plain FP32 path (per step permute + SIMT GEMM, one slice per launch)
+    plain_steps = max(1, args.plain_steps)
+    step(0, mode="plain", sb=1)
+    torch.cuda.synchronize()
+    p0 = torch.cuda.Event(enable_timing=True)
+    p1 = torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for i in range(plain_steps):
+        step(i, mode="plain", sb=1)
+    p1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = p0.elapsed_time(p1)
+    plain_sps = plain_steps / (plain_ms / 1e3)
+    plain_tflops = plain_sps * flops_per_slice / 1e12
+
+    # e2e: the public call with a host output buffer (D2H + sync inside)
+    host = np.zeros(2 * nb)
+    step(0, host_out=host)
+    t0 = time.perf_counter()
+    e2e_steps = max(1, min(args.steps, 5))
+    for i in range(e2e_steps):
+        step(i, host_out=host)
+    e2e_s = time.perf_counter() - t0
+    e2e_sps = e2e_steps * SB / e2e_s * world
+
+    # per-launch timings of one batch -> roofline of the dominant kernel
+    recs = P.tn_plan_profile(plan, base, prec="fp32", mode="fused", stream=stream)
+    by_kind = {}
+    for r in recs:
+        k = {0: "pass", 1: "gemm", 2: "permute", 3: "slice_sum"}[r["kind"]]
+        d = by_kind.setdefault(k, {"ms": 0.0, "bytes": 0.0, "flops": 0.0, "launches": 0})
+        d["ms"] += r["ms"]
+        d["bytes"] += r["bytes"]
+        d["flops"] += r["flops"]
+        d["launches"] += 1
+    dom = max(by_kind, key=lambda k: by_kind[k]["ms"])
+    peaks, peak_kind = measured_peaks()
+    d = by_kind[dom]
+    achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
+    tot_ms = sum(v["ms"] for v in by_kind.values())
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": "pass_kernel",
+                "peak_source": peak_kind, "share_of_step": d["ms"] / tot_ms if tot_ms else None,
+                "simt_tflops": d["flops"] / (d["ms"] / 1e3) / 1e12}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        order, sl = P.tn_plan_export(plan)
+        _, _, q, s = net.info()
+        wires = [(int(q[e]), int(s[e])) for e in sl]
+        tc, secs, done = oracle_sample(name, args.cpu_budget, order, wires, info)
+        cpu_tflops = 8.0 * tc / secs / 1e12
+        cpu = {"value": cpu_tflops, "unit": "TFLOP/s", "cores": oracle_threads(), "kind": "oracle",
+               "slices_per_s": tc / info["stem_tc_per_slice"] / secs,
+               "sample": f"FP64 pairwise contractions of slice 0 along the plan's order: "
+                         f"first {done} of {len(order)} pairs in {secs:.1f} s"}
+
+    launches_per_step = (info["n_passes_fused"] + info["n_gemm_steps"] + 2) + 1  # +finalize
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": tflops, "unit": "TFLOP/s",
+            "slices_per_s": slices_per_s, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": name, "n_qubits": c.n_qubits, "cycles": c.n_cycles,
+                       "n_open": len(oq), "cw": info["cw"], "n_sliced": info["n_sliced"],
+                       "stem_steps": info["n_stem_steps"], "fused_passes": info["n_passes_fused"],
+                       "slices_per_step": SB, "stem_tc_per_slice": info["stem_tc_per_slice"],
+                       "log2_tc_total": info["log2_tc"],
+                       "l2": "inputs larger than L2 (stem tensors up to 8 GiB)",
+                       "parallelism": f"slice ranges per GPU x{world}", "plan_seconds": plan_s},
+            "plain_fp32": {"value": plain_tflops, "unit": "TFLOP/s", "slices_per_s": plain_sps,
+                           "steps": plain_steps},
+            "speedup_vs_plain": slices_per_s / plain_sps / world if plain_sps else None,
+            "e2e": {"value": e2e_sps * flops_per_slice / 1e12, "unit": "TFLOP/s",
+                    "slices_per_s": e2e_sps, "h2d_bytes_per_step": 16,
+                    "d2h_bytes_per_step": 16 * nb},
+            "roofline": roofline,
+            "launch_breakdown": by_kind,
+            "cpu_baseline": cpu,
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clocks,
+            "amp_norm_check": float(np.linalg.norm(amps)),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,224 @@
+/*
+ * tnstem: stem contraction of random-circuit tensor networks on one GB300.
+ *
+ * C interface of libtnstem.so. Every entry point returns a tn_status and never
+ * throws; tn_last_error() gives the calling thread's last message.
+ *
+ * What the library computes (paper: "Classical Simulation of Quantum
+ * Supremacy Circuits", Huang et al., arXiv:2005.06787):
+ *   - the tensor network of a Sycamore-style random circuit (Sec. 2, Sec. 3);
+ *   - a slicing-incorporated contraction scheme (E_s, T) (Supp. A.1,
+ *     "Slicing") whose contraction tree has a stem and branches (Sec. 4,
+ *     Supp. A.2), found by stem growth, local optimisation and dynamic
+ *     slicing (Sec. 4, Supp. A.2), or given by the caller;
+ *   - for a range of slices, the sum of the sub-network values (Supp. A.1):
+ *     the amplitudes of a batch of bitstrings whose open qubits take every
+ *     assignment (Sec. 3, "open tensor network", 64 amplitudes for 6 open
+ *     qubits), with branches pre-computed once (Supp. A.3).
+ *
+ * Conventions.
+ *   Qubits are 0..n-1. A bitstring prefix gives one bit per closed qubit
+ *   (qubits not listed as open), in ascending qubit order.
+ *   Amplitude index: the open qubits in the order given, first one = most
+ *   significant bit. Amplitudes are returned as interleaved (re, im) doubles.
+ *   Edges of the network are wire segments (q, s): segment s of qubit q
+ *   follows the s-th gate acting on q (segment 0 follows |0>).
+ *   Leaves are numbered: |0> on qubits 0..n-1; then per cycle t < m the
+ *   single-qubit gates of layer t on qubits 0..n-1 followed by the two-qubit
+ *   gates of layer t in listed order; then the final single-qubit layer; then
+ *   one projector per closed qubit, ascending. An order is an SSA pair list:
+ *   the k-th pair creates node n_leaves + k.
+ *   Slice id s fixes sliced edge j (in the plan's sliced list) to bit j of s.
+ *
+ * Ownership. Handles are opaque and owned by the library until destroyed.
+ * Input arrays are copied. Output arrays are owned by the caller.
+ */
+#ifndef TNSTEM_H
+#define TNSTEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TN_OK = 0,
+    TN_ERR_INVALID_ARG = 1,     /* bad pointer, size, range, order or edge */
+    TN_ERR_OOM = 2,             /* device or host allocation failed */
+    TN_ERR_CUDA = 3,            /* a CUDA call failed (message has the name) */
+    TN_ERR_PLAN_INFEASIBLE = 4, /* no scheme within the width limit */
+    TN_ERR_TIMEOUT = 5,         /* a bounded device wait ran out */
+    TN_ERR_UNSUPPORTED = 6      /* shape outside what the kernels handle */
+} tn_status;
+
+/* Arithmetic of the stem's GEMM steps (Sec. 6 notes tensor cores were left
+ * unused by the paper; these are this library's options). Fused memory-bound
+ * passes always compute in FP32 on the CUDA cores. */
+typedef enum {
+    TN_PREC_FP32_SIMT = 0, /* FP32 FMA on CUDA cores */
+    TN_PREC_TF32x3 = 1,    /* tcgen05, split TF32 hi/lo, 3 products, FP32 accumulate */
+    TN_PREC_BF16x3 = 2,    /* tcgen05, split BF16 hi/lo, 3 products, FP32 accumulate */
+    TN_PREC_BF16x1 = 3     /* tcgen05, one BF16 product, FP32 accumulate */
+} tn_precision;
+
+/* How the stem is executed. */
+typedef enum {
+    TN_EXEC_PLAIN = 0, /* per stem step: a permute then a complex GEMM, one slice per launch */
+    TN_EXEC_FUSED = 1  /* consecutive steps fused into one HBM pass, slices batched, graph replay */
+} tn_exec_mode;
+
+typedef struct {
+    int32_t n_qubits;
+    int32_t n_cycles;            /* m */
+    const int8_t *gates_1q;      /* (m+1) * n_qubits ids: 0 sqrt(X), 1 sqrt(Y), 2 sqrt(W) */
+    const int32_t *pair_offsets; /* m + 1 offsets into pairs (in pairs, not ints) */
+    const int32_t *pairs;        /* flattened (qa, qb), qa < qb, per two-qubit layer */
+    double theta, phi;           /* fSim parameters, the same on every coupler */
+} tn_circuit;
+
+typedef struct tn_network tn_network;
+typedef struct tn_plan tn_plan;
+
+typedef struct {
+    int32_t cw_limit;         /* max log2 entries of any intermediate tensor, e.g. 30 */
+    int32_t min_sliced;       /* slice at least this many edges (0 = only as needed) */
+    int32_t max_sliced;       /* give up beyond this many sliced edges */
+    int32_t restarts;         /* randomised stem-growth restarts */
+    int32_t local_opt_iters;  /* local-optimisation sweeps before/between/after slicing */
+    int32_t branch_rank;      /* max rank of a branch cluster (default 4) */
+    int32_t slice_batch;      /* batch items per launch in fused mode (0 = auto) */
+    int32_t tile_bits;        /* fused-pass tile size log2 (0 = auto, <= 12) */
+    int32_t max_pass_steps;   /* steps fused into one pass (0 = auto) */
+    int32_t gemm_min_kn;      /* steps with k or n >= this run as GEMM (0 = auto) */
+    uint64_t seed;
+} tn_plan_opts;
+
+typedef struct {
+    double log2_tc;           /* log2 tc((E_s, T)) over all slices */
+    double stem_tc_per_slice; /* sum over stem steps of 2^|E_u|, one slice */
+    double branch_tc;         /* pre-computation cost, once per prefix */
+    int32_t cw;               /* contraction width (sliced) */
+    int32_t n_sliced;
+    int32_t n_stem_steps;
+    int32_t n_branches;
+    int32_t n_passes_fused;
+    int32_t n_gemm_steps;     /* steps run as a GEMM in fused mode */
+    int32_t n_open;
+    int32_t n_prefixes;
+    int32_t batch_items;      /* items (prefix, slice) per fused launch */
+    double stem_bytes_plain;  /* algorithmic HBM bytes per slice, plain mode */
+    double stem_bytes_fused;  /* algorithmic HBM bytes per slice, fused mode */
+    double max_stem_elems;    /* largest stem tensor, entries */
+    int64_t device_bytes;     /* device memory held by the plan */
+} tn_plan_stats;
+
+/* One stem step as the plan runs it (features for cost models). */
+typedef struct {
+    int32_t r_in, r_out;      /* stem rank before / after */
+    int32_t k, n;             /* contracted / new bits: C[m,n] = sum_k S[m,k] B[k,n] */
+    int32_t pass;             /* fused pass index holding this step (-1: GEMM step) */
+    int32_t gemm;             /* 1 if run as a tensor-core GEMM in fused mode */
+} tn_step_info;
+
+/* Sec. 2-3: build the network of circuit c with the listed open qubits and the
+ * closed qubits projected on closed_bits (n_qubits - n_open bytes, 0/1).
+ * No device work. */
+tn_status tn_build_network(const tn_circuit *c, const int32_t *open_qubits, int32_t n_open,
+                           const uint8_t *closed_bits, tn_network **out);
+
+/* Number of leaves and edges; edge e is wire segment (qubit[e], segment[e]).
+ * Any output pointer may be NULL; arrays hold n_edges entries. */
+tn_status tn_network_info(const tn_network *net, int32_t *n_leaves, int32_t *n_edges,
+                          int32_t *qubit, int32_t *segment);
+
+/* Supp. A.1-A.2: make a contraction scheme. order (n_pairs = n_leaves - 1
+ * SSA pairs) may be NULL: the planner then grows a stem (Sec. 4). sliced_edges
+ * may be NULL: the planner then slices greedily (Supp. A.2, "Dynamic slicing")
+ * until the width is within opts->cw_limit. Host-only; no device work. */
+tn_status tn_plan_create(tn_network *net, const int32_t *order, int32_t n_pairs,
+                         const int32_t *sliced_edges, int32_t n_sliced,
+                         const tn_plan_opts *opts, tn_plan **out);
+
+/* Upload leaves for n_prefixes bitstring prefixes (n_prefixes * n_closed
+ * bytes; NULL = the network's own prefix) and pre-compute every branch on
+ * the device, once (Supp. A.3, "Pre-computation"). Allocates device memory.
+ * Must precede tn_contract_stem; may be called again to change prefixes. */
+tn_status tn_plan_prepare(tn_plan *plan, const uint8_t *prefixes, int32_t n_prefixes,
+                          void *cuda_stream);
+
+tn_status tn_plan_info(const tn_plan *plan, tn_plan_stats *out);
+
+/* Export the scheme: order (2*(n_leaves-1) ints, SSA pairs over the leaves),
+ * sliced edge ids (n_sliced ints, slice-bit order). Either may be NULL. */
+tn_status tn_plan_export(const tn_plan *plan, int32_t *order, int32_t *sliced_edges);
+
+/* Per-step shapes; writes min(max_steps, n_stem_steps) records. */
+tn_status tn_plan_steps(const tn_plan *plan, tn_step_info *out, int32_t max_steps,
+                        int32_t *n_written);
+
+/* Supp. A.1 "Slicing": contract slices [slice_begin, slice_end) for every
+ * prepared prefix and add their values. amps_out holds n_prefixes * 2^n_open
+ * (re, im) doubles, prefix-major; host or device memory. With accumulate != 0
+ * the result is added to amps_out. The slice sum is kept in FP64 with
+ * Neumaier compensation on the device, so disjoint ranges add. Asynchronous
+ * on cuda_stream when amps_out is device memory; synchronises otherwise.
+ * slice_end <= 2^n_sliced, else TN_ERR_INVALID_ARG. */
+tn_status tn_contract_stem(tn_plan *plan, uint64_t slice_begin, uint64_t slice_end,
+                           tn_precision prec, tn_exec_mode mode, void *cuda_stream,
+                           double *amps_out, int32_t accumulate);
+
+/* One kernel launch of a profiled batch. */
+typedef struct {
+    int32_t kind;     /* 0 fused pass, 1 GEMM step, 2 permute (plain), 3 slice sum */
+    int32_t index;    /* position in the batch's launch sequence */
+    int32_t r_in, r_out;
+    int32_t n_steps;  /* stem steps applied by this launch */
+    int32_t k, n;     /* GEMM steps: contracted / new bits */
+    int32_t items;    /* batch items (prefix, slice) processed */
+    double ms;        /* CUDA-event duration on the launch stream */
+    double bytes;     /* algorithmic HBM bytes: 8 * (2^r_in + 2^r_out) per item */
+    double flops;     /* algorithmic flops: 8 * sum of 2^|E_u| over its steps, per item */
+} tn_launch_record;
+
+/* Run one batch starting at slice_begin launch by launch, timing each launch
+ * with CUDA events on cuda_stream (per-step timing, Supp. A.4 "explicit
+ * simulations of subtasks"). Writes up to max_records records; n_records
+ * receives the count. Synchronises cuda_stream. */
+tn_status tn_plan_profile(tn_plan *plan, uint64_t slice_begin, tn_precision prec,
+                          tn_exec_mode mode, void *cuda_stream, tn_launch_record *out,
+                          int32_t max_records, int32_t *n_records);
+
+void tn_plan_destroy(tn_plan *plan);
+void tn_network_destroy(tn_network *net);
+
+/* Sec. 2: linear XEB 2^n <p> - 1 of count amplitudes (interleaved re, im,
+ * device memory), p = |amp|^2, computed in FP64 on the device. out is a host
+ * double. Synchronises cuda_stream. */
+tn_status tn_linear_xeb(const double *amps_dev, int64_t count, int32_t n_qubits,
+                        void *cuda_stream, double *out);
+
+/* ---- single kernels, for tests and tuning (device pointers, complex64 as
+ * interleaved float pairs) ---- */
+
+/* Bit permutation of a 2^rank tensor: input bit j moves to output bit
+ * perm[j]. Supp. A.1 "up to transposition". */
+tn_status tn_permute(const float *in, float *out, int32_t rank, const int32_t *perm,
+                     void *cuda_stream);
+
+/* Complex GEMM C[b][m][n] = sum_k A[b][m][k] * B[b][k][n], row-major, batch
+ * strides in complex elements (0 broadcasts). One stem step, Supp. A.1
+ * (a pairwise contraction is a GEMM after permutation). */
+tn_status tn_cgemm(const float *A, const float *B, float *C, int64_t M, int64_t K, int64_t N,
+                   int64_t batch, int64_t strideA, int64_t strideB, int64_t strideC,
+                   tn_precision prec, void *cuda_stream);
+
+const char *tn_last_error(void);
+const char *tn_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TNSTEM_H */

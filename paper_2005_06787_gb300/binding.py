@@ -1,0 +1,313 @@
+"""ctypes binding of libtnstem.so: the C entry points under the same names.
+
+Argument marshalling only; every step of the stem runs in the library's CUDA
+kernels. Loading fails loudly when the library has not been built.
+PyTorch supplies device memory (tensors) and streams.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libtnstem.so")
+
+TN_OK = 0
+STATUS_NAMES = {0: "TN_OK", 1: "TN_ERR_INVALID_ARG", 2: "TN_ERR_OOM", 3: "TN_ERR_CUDA",
+                4: "TN_ERR_PLAN_INFEASIBLE", 5: "TN_ERR_TIMEOUT", 6: "TN_ERR_UNSUPPORTED"}
+
+PREC = {"fp32": 0, "tf32x3": 1, "bf16x3": 2, "bf16x1": 3}
+MODE = {"plain": 0, "fused": 1}
+
+EXPORTED = [
+    "tn_build_network", "tn_network_info", "tn_plan_create", "tn_plan_prepare", "tn_plan_info",
+    "tn_plan_export", "tn_plan_steps", "tn_contract_stem", "tn_plan_profile", "tn_plan_destroy",
+    "tn_network_destroy", "tn_linear_xeb", "tn_permute", "tn_cgemm", "tn_last_error",
+    "tn_version",
+]
+
+
+class TnError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class tn_circuit(C.Structure):
+    _fields_ = [("n_qubits", C.c_int32), ("n_cycles", C.c_int32),
+                ("gates_1q", C.POINTER(C.c_int8)), ("pair_offsets", C.POINTER(C.c_int32)),
+                ("pairs", C.POINTER(C.c_int32)), ("theta", C.c_double), ("phi", C.c_double)]
+
+
+class tn_plan_opts(C.Structure):
+    _fields_ = [("cw_limit", C.c_int32), ("min_sliced", C.c_int32), ("max_sliced", C.c_int32),
+                ("restarts", C.c_int32), ("local_opt_iters", C.c_int32),
+                ("branch_rank", C.c_int32), ("slice_batch", C.c_int32),
+                ("tile_bits", C.c_int32), ("max_pass_steps", C.c_int32),
+                ("gemm_min_kn", C.c_int32), ("seed", C.c_uint64)]
+
+
+class tn_plan_stats(C.Structure):
+    _fields_ = [("log2_tc", C.c_double), ("stem_tc_per_slice", C.c_double),
+                ("branch_tc", C.c_double), ("cw", C.c_int32), ("n_sliced", C.c_int32),
+                ("n_stem_steps", C.c_int32), ("n_branches", C.c_int32),
+                ("n_passes_fused", C.c_int32), ("n_gemm_steps", C.c_int32),
+                ("n_open", C.c_int32), ("n_prefixes", C.c_int32), ("batch_items", C.c_int32),
+                ("stem_bytes_plain", C.c_double), ("stem_bytes_fused", C.c_double),
+                ("max_stem_elems", C.c_double), ("device_bytes", C.c_int64)]
+
+
+class tn_step_info(C.Structure):
+    _fields_ = [("r_in", C.c_int32), ("r_out", C.c_int32), ("k", C.c_int32), ("n", C.c_int32),
+                ("pass_", C.c_int32), ("gemm", C.c_int32)]
+
+
+class tn_launch_record(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("index", C.c_int32), ("r_in", C.c_int32),
+                ("r_out", C.c_int32), ("n_steps", C.c_int32), ("k", C.c_int32), ("n", C.c_int32),
+                ("items", C.c_int32), ("ms", C.c_double), ("bytes", C.c_double),
+                ("flops", C.c_double)]
+
+
+_lib = None
+
+
+def load():
+    """Load libtnstem.so; raise if it was not built (no fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libtnstem.so not built at {LIB_PATH}: run "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    L = C.CDLL(LIB_PATH)
+    vp, i32, i64, u64 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64
+    L.tn_build_network.argtypes = [C.POINTER(tn_circuit), vp, i32, vp, C.POINTER(vp)]
+    L.tn_network_info.argtypes = [vp, vp, vp, vp, vp]
+    L.tn_plan_create.argtypes = [vp, vp, i32, vp, i32, C.POINTER(tn_plan_opts), C.POINTER(vp)]
+    L.tn_plan_prepare.argtypes = [vp, vp, i32, vp]
+    L.tn_plan_info.argtypes = [vp, C.POINTER(tn_plan_stats)]
+    L.tn_plan_export.argtypes = [vp, vp, vp]
+    L.tn_plan_steps.argtypes = [vp, vp, i32, vp]
+    L.tn_contract_stem.argtypes = [vp, u64, u64, C.c_int, C.c_int, vp, vp, i32]
+    L.tn_plan_destroy.argtypes = [vp]
+    L.tn_plan_destroy.restype = None
+    L.tn_network_destroy.argtypes = [vp]
+    L.tn_network_destroy.restype = None
+    L.tn_plan_profile.argtypes = [vp, u64, C.c_int, C.c_int, vp, vp, i32, vp]
+    L.tn_linear_xeb.argtypes = [vp, i64, i32, vp, C.POINTER(C.c_double)]
+    L.tn_permute.argtypes = [vp, vp, i32, vp, vp]
+    L.tn_cgemm.argtypes = [vp, vp, vp, i64, i64, i64, i64, i64, i64, i64, C.c_int, vp]
+    L.tn_last_error.restype = C.c_char_p
+    L.tn_last_error.argtypes = []
+    L.tn_version.restype = C.c_char_p
+    L.tn_version.argtypes = []
+    for name in EXPORTED:
+        if name not in ("tn_plan_destroy", "tn_network_destroy", "tn_last_error", "tn_version"):
+            getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _check(status: int):
+    if status != TN_OK:
+        raise TnError(status, load().tn_last_error().decode())
+
+
+def _ptr(a) -> int:
+    """Address of a torch tensor or numpy array (None -> 0)."""
+    if a is None:
+        return 0
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            pass
+        return 0
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# --------------------------------------------------------------------- network
+
+class Network:
+    def __init__(self, handle, n_open: int, n_closed: int, keep):
+        self.handle = handle
+        self.n_open = n_open
+        self.n_closed = n_closed
+        self._keep = keep
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.tn_network_destroy(self.handle)
+            self.handle = None
+
+    def info(self) -> Tuple[int, int, np.ndarray, np.ndarray]:
+        L = load()
+        nl, ne = C.c_int32(), C.c_int32()
+        _check(L.tn_network_info(self.handle, C.byref(nl), C.byref(ne), None, None))
+        q = np.zeros(ne.value, dtype=np.int32)
+        s = np.zeros(ne.value, dtype=np.int32)
+        _check(L.tn_network_info(self.handle, None, None, q.ctypes.data, s.ctypes.data))
+        return nl.value, ne.value, q, s
+
+
+def tn_build_network(circuit, open_qubits: Sequence[int], closed_bits: Sequence[int]) -> Network:
+    L = load()
+    g, offs, pairs = circuit.flat()
+    g = np.ascontiguousarray(g.reshape(-1), dtype=np.int8)
+    c = tn_circuit(circuit.n_qubits, circuit.n_cycles,
+                   g.ctypes.data_as(C.POINTER(C.c_int8)),
+                   offs.ctypes.data_as(C.POINTER(C.c_int32)),
+                   pairs.ctypes.data_as(C.POINTER(C.c_int32)), circuit.theta, circuit.phi)
+    oq = np.asarray(list(open_qubits) or [0], dtype=np.int32)
+    cb = np.asarray(list(closed_bits) or [0], dtype=np.uint8)
+    h = C.c_void_p()
+    _check(L.tn_build_network(C.byref(c), oq.ctypes.data, len(open_qubits), cb.ctypes.data,
+                              C.byref(h)))
+    return Network(h, len(open_qubits), circuit.n_qubits - len(open_qubits), (g, offs, pairs))
+
+
+# ------------------------------------------------------------------------ plan
+
+def make_opts(**kw) -> tn_plan_opts:
+    o = tn_plan_opts()
+    defaults = dict(cw_limit=30, min_sliced=0, max_sliced=40, restarts=8, local_opt_iters=4,
+                    branch_rank=4, slice_batch=0, tile_bits=0, max_pass_steps=0, gemm_min_kn=0,
+                    seed=0x5EED)
+    defaults.update(kw)
+    for k, v in defaults.items():
+        setattr(o, k, int(v))
+    return o
+
+
+class Plan:
+    def __init__(self, handle, net: Network):
+        self.handle = handle
+        self.net = net
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.tn_plan_destroy(self.handle)
+            self.handle = None
+
+    def info(self) -> dict:
+        return tn_plan_info(self)
+
+
+def tn_plan_create(net: Network, order: Optional[Sequence[Tuple[int, int]]] = None,
+                   sliced_edges: Optional[Sequence[int]] = None, **opts) -> Plan:
+    L = load()
+    o = make_opts(**opts)
+    ordp, n_pairs = None, 0
+    if order is not None:
+        ordp = np.ascontiguousarray(np.asarray(order, dtype=np.int32).reshape(-1))
+        n_pairs = len(order)
+    slp, nsl = None, 0
+    if sliced_edges is not None and len(sliced_edges):
+        slp = np.ascontiguousarray(np.asarray(sliced_edges, dtype=np.int32))
+        nsl = len(sliced_edges)
+    h = C.c_void_p()
+    _check(L.tn_plan_create(net.handle, _ptr(ordp) or None, n_pairs, _ptr(slp) or None, nsl,
+                            C.byref(o), C.byref(h)))
+    return Plan(h, net)
+
+
+def tn_plan_prepare(plan: Plan, prefixes: Optional[np.ndarray] = None, stream=None):
+    L = load()
+    if prefixes is None:
+        _check(L.tn_plan_prepare(plan.handle, None, 0, _stream(stream)))
+        return
+    pre = np.ascontiguousarray(np.asarray(prefixes, dtype=np.uint8))
+    if pre.ndim == 1:
+        pre = pre[None, :]
+    _check(L.tn_plan_prepare(plan.handle, pre.ctypes.data, pre.shape[0], _stream(stream)))
+
+
+def tn_plan_info(plan: Plan) -> dict:
+    L = load()
+    s = tn_plan_stats()
+    _check(L.tn_plan_info(plan.handle, C.byref(s)))
+    return {f: getattr(s, f) for f, _ in tn_plan_stats._fields_}
+
+
+def tn_plan_export(plan: Plan) -> Tuple[np.ndarray, np.ndarray]:
+    L = load()
+    nl, _, _, _ = plan.net.info()
+    info = tn_plan_info(plan)
+    order = np.zeros(2 * (nl - 1), dtype=np.int32)
+    sl = np.zeros(max(info["n_sliced"], 1), dtype=np.int32)
+    _check(L.tn_plan_export(plan.handle, order.ctypes.data, sl.ctypes.data))
+    return order.reshape(-1, 2), sl[:info["n_sliced"]]
+
+
+def tn_plan_steps(plan: Plan):
+    L = load()
+    n = C.c_int32()
+    _check(L.tn_plan_steps(plan.handle, None, 0, C.byref(n)))
+    arr = (tn_step_info * max(n.value, 1))()
+    w = C.c_int32()
+    _check(L.tn_plan_steps(plan.handle, arr, n.value, C.byref(w)))
+    return [dict(r_in=a.r_in, r_out=a.r_out, k=a.k, n=a.n, pass_=a.pass_, gemm=a.gemm)
+            for a in arr[:w.value]]
+
+
+def tn_contract_stem(plan: Plan, slice_begin: int, slice_end: int, out, prec: str = "fp32",
+                     mode: str = "fused", stream=None, accumulate: bool = False):
+    """out: float64 tensor/array of n_prefixes * 2^n_open * 2 (re, im)."""
+    L = load()
+    _check(L.tn_contract_stem(plan.handle, int(slice_begin), int(slice_end), PREC[prec],
+                              MODE[mode], _stream(stream), _ptr(out), int(bool(accumulate))))
+    return out
+
+
+def tn_plan_profile(plan: Plan, slice_begin: int = 0, prec: str = "fp32", mode: str = "fused",
+                    stream=None):
+    """Per-launch CUDA-event timings of one batch (list of dicts)."""
+    L = load()
+    n = C.c_int32()
+    arr = (tn_launch_record * 4096)()
+    _check(L.tn_plan_profile(plan.handle, int(slice_begin), PREC[prec], MODE[mode], _stream(stream),
+                             arr, 4096, C.byref(n)))
+    return [{f: getattr(a, f) for f, _ in tn_launch_record._fields_} for a in arr[:n.value]]
+
+
+def tn_linear_xeb(amps_dev, n_qubits: int, stream=None) -> float:
+    L = load()
+    out = C.c_double()
+    count = amps_dev.numel() // 2
+    _check(L.tn_linear_xeb(_ptr(amps_dev), count, n_qubits, _stream(stream), C.byref(out)))
+    return out.value
+
+
+def tn_permute(inp, out, rank: int, perm: Sequence[int], stream=None):
+    L = load()
+    p = np.ascontiguousarray(np.asarray(perm, dtype=np.int32))
+    _check(L.tn_permute(_ptr(inp), _ptr(out), rank, p.ctypes.data, _stream(stream)))
+    return out
+
+
+def tn_cgemm(A, B, Cm, M: int, K: int, N: int, batch: int = 1, strideA: int = 0,
+             strideB: int = 0, strideC: int = 0, prec: str = "fp32", stream=None):
+    L = load()
+    _check(L.tn_cgemm(_ptr(A), _ptr(B), _ptr(Cm), M, K, N, batch, strideA, strideB, strideC,
+                      PREC[prec], _stream(stream)))
+    return Cm
+
+
+def tn_version() -> str:
+    return load().tn_version().decode()

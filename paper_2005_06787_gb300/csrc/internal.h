@@ -1,0 +1,260 @@
+// Internal data structures of libtnstem: network, contraction scheme, stem
+// plan and the device descriptors the kernels read.
+#pragma once
+
+#include <complex>
+#include <cstdint>
+#include <random>
+#include <string>
+#include <vector>
+
+#include "../../include/tnstem.h"
+
+namespace tn {
+
+using cd = std::complex<double>;
+
+// ----------------------------------------------------------------- errors
+struct Error {
+    tn_status code;
+    std::string msg;
+};
+[[noreturn]] void fail(tn_status code, const std::string &msg);
+void set_last_error(const std::string &msg);
+
+// ----------------------------------------------------------------- bitset
+struct Bits {
+    std::vector<uint64_t> w;
+    Bits() = default;
+    explicit Bits(int nbits) : w((size_t)((nbits + 63) / 64), 0ull) {}
+    void set(int i) { w[(size_t)i >> 6] |= 1ull << (i & 63); }
+    void reset(int i) { w[(size_t)i >> 6] &= ~(1ull << (i & 63)); }
+    bool test(int i) const { return (w[(size_t)i >> 6] >> (i & 63)) & 1ull; }
+    int count() const {
+        int c = 0;
+        for (uint64_t x : w) c += __builtin_popcountll(x);
+        return c;
+    }
+    Bits &operator^=(const Bits &o) {
+        for (size_t i = 0; i < w.size(); ++i) w[i] ^= o.w[i];
+        return *this;
+    }
+    Bits &operator|=(const Bits &o) {
+        for (size_t i = 0; i < w.size(); ++i) w[i] |= o.w[i];
+        return *this;
+    }
+    Bits &operator&=(const Bits &o) {
+        for (size_t i = 0; i < w.size(); ++i) w[i] &= o.w[i];
+        return *this;
+    }
+    Bits andnot(const Bits &o) const {
+        Bits r = *this;
+        for (size_t i = 0; i < w.size(); ++i) r.w[i] &= ~o.w[i];
+        return r;
+    }
+    bool any() const {
+        for (uint64_t x : w)
+            if (x) return true;
+        return false;
+    }
+    bool operator==(const Bits &o) const { return w == o.w; }
+    std::vector<int> list() const {
+        std::vector<int> r;
+        for (size_t i = 0; i < w.size(); ++i) {
+            uint64_t x = w[i];
+            while (x) {
+                int b = __builtin_ctzll(x);
+                r.push_back((int)(i * 64 + b));
+                x &= x - 1;
+            }
+        }
+        return r;
+    }
+};
+inline Bits operator^(Bits a, const Bits &b) { return a ^= b; }
+inline Bits operator|(Bits a, const Bits &b) { return a |= b; }
+inline Bits operator&(Bits a, const Bits &b) { return a &= b; }
+inline int count_and(const Bits &a, const Bits &b) {
+    int c = 0;
+    for (size_t i = 0; i < a.w.size(); ++i) c += __builtin_popcountll(a.w[i] & b.w[i]);
+    return c;
+}
+inline int count_or(const Bits &a, const Bits &b) {
+    int c = 0;
+    for (size_t i = 0; i < a.w.size(); ++i) c += __builtin_popcountll(a.w[i] | b.w[i]);
+    return c;
+}
+inline int count_xor(const Bits &a, const Bits &b) {
+    int c = 0;
+    for (size_t i = 0; i < a.w.size(); ++i) c += __builtin_popcountll(a.w[i] ^ b.w[i]);
+    return c;
+}
+
+// ----------------------------------------------------------------- network
+enum LeafKind { LEAF_ZERO = 0, LEAF_1Q = 1, LEAF_2Q = 2, LEAF_PROJ = 3 };
+
+struct Leaf {
+    int kind;
+    int qa, qb;              // qubits (qb = -1 for one-qubit leaves)
+    int gate;                // single-qubit gate id, or closed index for projectors
+    std::vector<int> edges;  // edge at bit position j of the value index
+    std::vector<cd> vals;    // 2^rank values, index = sum_j a_{edges[j]} 2^j
+};
+
+struct EdgeInfo {
+    int qubit, segment;
+    int ends[2];
+    int n_ends;
+    bool open;
+};
+
+struct Network {
+    int n_qubits = 0, n_cycles = 0;
+    double theta = 0, phi = 0;
+    std::vector<Leaf> leaves;
+    std::vector<EdgeInfo> edges;
+    std::vector<int> open_qubits, open_edges;  // open_edges[i] belongs to open_qubits[i]
+    std::vector<int> closed_qubits;
+    std::vector<uint8_t> closed_bits;
+    std::vector<int> proj_leaf;  // leaf id of the projector of closed qubit i
+    int n_edges() const { return (int)edges.size(); }
+    int n_leaves() const { return (int)leaves.size(); }
+};
+
+Network build_network(const tn_circuit &c, const int32_t *open_qubits, int n_open,
+                      const uint8_t *closed_bits);
+void gate_matrix_1q(int id, cd out[4]);
+void fsim_matrix(double theta, double phi, cd out[16]);
+
+// ----------------------------------------------------------------- scheme
+// A subtree is a list of SSA-style pairs over "refs": ref >= 0 is a leaf id,
+// ref < 0 is -(j+1) for the j-th pair of the same list.
+using PairList = std::vector<std::pair<int, int>>;
+
+struct Cluster {
+    std::vector<int> leaves;
+    PairList pairs;  // internal pairs (leaves.size() - 1 of them)
+    Bits out;        // output edges over the full network (sliced included)
+};
+
+// One stem step: the stem absorbs cluster `branch`.
+struct StemStep {
+    int branch;
+    std::vector<int> K;     // contracted edges (stem ∩ branch), unsliced
+    std::vector<int> Nnew;  // new edges (branch \ stem), unsliced
+    int r_in, r_out;        // stem ranks (unsliced) before/after
+};
+
+struct Scheme {
+    std::vector<Cluster> clusters;
+    int seed_cluster = -1;
+    std::vector<int> stem_order;  // clusters absorbed by the stem, in order
+    Bits sliced;
+    std::vector<int> sliced_list;  // in slice-bit order
+    double log2_tc = 0, stem_tc = 0, branch_tc = 0;
+    int cw = 0;
+};
+
+// cost helpers
+double log2_add(double a, double b);
+struct StemCost {
+    double tc = 0;      // sum of 2^|E_u| over stem steps (unsliced edges only)
+    int max_rank = 0;   // max |E*_u| over stem tensors
+};
+
+Scheme plan_scheme(const Network &net, const tn_plan_opts &opts);
+Scheme scheme_from_order(const Network &net, const std::vector<std::pair<int, int>> &order,
+                         const std::vector<int> &sliced, const tn_plan_opts &opts);
+void evaluate_scheme(const Network &net, Scheme &s);
+std::vector<std::pair<int, int>> export_order(const Network &net, const Scheme &s);
+
+// ----------------------------------------------------------------- device plan
+constexpr int MAX_PASS_STEPS = 8;
+constexpr int MAX_STEP_K = 4;    // k, n <= 4 inside fused passes
+constexpr int MAX_TILE_BITS = 12;
+constexpr int MAX_BRANCH_SLICED = 24;
+constexpr int MAX_FREE = 40;
+
+// All offsets are in complex elements.
+struct DevStep {
+    int k, n, rest;
+    int branch;                 // index into DevBranch table
+    int koff[16], noff[16];     // tile offsets of kappa / nu bits
+    int in_lo[64], in_hi[64];   // rest index -> input tile offset
+    int out_lo[64], out_hi[64]; // rest index -> output tile offset
+};
+
+struct DevBranch {
+    int64_t base;           // offset into the branch pool
+    int64_t prefix_stride;  // 0 when independent of the prefix
+    int k, n;               // matrix rows 2^k (kappa), cols 2^n (nu); nu fastest
+    int n_sl;               // sliced edges stored as dims
+    int sl_bit[MAX_BRANCH_SLICED];  // slice-id bit of each
+    int sl_pos[MAX_BRANCH_SLICED];  // storage bit position of each
+};
+
+// 16-byte aligned: kernels copy it to shared memory with 16-byte loads.
+struct alignas(16) DevPass {
+    int r_in, r_out;
+    int t_in, t_out;        // tile bits in / out
+    int c_in, c_out;        // contiguous chunk bits in / out
+    int n_free;
+    int tile_max;           // max tile entries over the pass's states
+    int n_steps;
+    int in_branch;          // >= 0: input is this branch's storage (seed)
+    int64_t in_item_stride, out_item_stride;
+    int64_t n_tiles;        // 2^n_free
+    int chunk_in_base, chunk_out_base;  // offsets into the chunk table
+    int64_t free_in[MAX_FREE], free_out[MAX_FREE];  // strides of free bits
+    DevStep steps[MAX_PASS_STEPS];
+};
+static_assert(sizeof(DevPass) % 16 == 0, "DevPass must be a multiple of 16 bytes");
+
+// Host-side description of the executable stem.
+struct ExecStep {  // plain mode: permute pass + GEMM
+    int permute_pass;   // index into plain passes
+    int branch;
+    int k, n;
+    int64_t M;          // 2^(r_in - k)
+    int r_in, r_out;
+};
+
+struct FusedItem {  // fused mode: either a pass or a GEMM step
+    int kind;           // 0 pass, 1 gemm (permute pass before it is a separate item)
+    int pass;           // index into fused passes
+    int branch, k, n;
+    int64_t M;
+    int r_in, r_out;
+};
+
+struct StemPlan {
+    // layouts: edge at each bit position
+    std::vector<std::vector<int>> plain_layouts;  // after each plain step
+    std::vector<DevPass> plain_passes;
+    std::vector<ExecStep> plain_steps;
+    std::vector<DevPass> fused_passes;
+    std::vector<FusedItem> fused_items;
+    std::vector<int> chunk_table;                 // chunk offsets of all passes
+    std::vector<int> final_layout_plain, final_layout_fused;
+    int max_rank = 0;
+    double bytes_plain = 0, bytes_fused = 0;
+    std::vector<int> step_pass;                   // fused pass of each stem step
+    std::vector<int> step_gemm;
+};
+
+// Branch storage layout chosen by the planner.
+struct BranchLayout {
+    std::vector<int> bits;  // edge at storage bit j (nu..., kappa..., sliced...)
+    int k = 0, n = 0;       // kappa / nu counts (seed: n = rank, k = 0)
+    bool prefix_dependent = false;
+    std::vector<int> sliced_edges;  // global edge ids at the top positions
+};
+
+struct BuiltStem {
+    StemPlan sp;
+    std::vector<BranchLayout> layouts;  // per cluster
+};
+
+struct Plan;  // defined in plan.h
+
+}  // namespace tn

@@ -1,0 +1,521 @@
+// CUDA kernels of the stem (sm_103a): fused multi-step pass, branch
+// pre-computation contraction, SIMT complex GEMM, FP64 compensated slice sum,
+// XEB reduction.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "kernels.h"
+
+namespace tn {
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ void cfma(float2 &acc, float2 a, float2 b) {
+    acc.x = fmaf(a.x, b.x, acc.x);
+    acc.x = fmaf(-a.y, b.y, acc.x);
+    acc.y = fmaf(a.x, b.y, acc.y);
+    acc.y = fmaf(a.y, b.x, acc.y);
+}
+
+// Offset (in complex entries) of branch storage for prefix p and slice s.
+__device__ __forceinline__ int64_t branch_offset(const DevBranch &b, int p, int64_t s) {
+    int64_t o = b.base + (int64_t)p * b.prefix_stride;
+    for (int i = 0; i < b.n_sl; ++i)
+        if ((s >> b.sl_bit[i]) & 1) o += (int64_t)1 << b.sl_pos[i];
+    return o;
+}
+
+// ---------------------------------------------------------------- fused pass
+// One stem step inside the tile: for each rest index rho (thread-strided),
+// y[nu] = sum_kappa x[kappa] * B[kappa][nu], read at in-tile offsets
+// io(rho) + koff[kappa], written at oo(rho) + noff[nu].
+template <int K, int N>
+__device__ __forceinline__ void step_body(const float2 *__restrict__ tin, float2 *__restrict__ tout,
+                                          const DevStep &S, const float2 *__restrict__ Bm, int nt) {
+    constexpr int NK = 1 << K, NN = 1 << N;
+    int koff[NK];
+#pragma unroll
+    for (int kk = 0; kk < NK; ++kk) koff[kk] = S.koff[kk];
+    const int nrest = 1 << S.rest;
+    for (int r = threadIdx.x; r < nrest; r += nt) {
+        const int io = S.in_lo[r & 63] + S.in_hi[r >> 6];
+        const int oo = S.out_lo[r & 63] + S.out_hi[r >> 6];
+        float2 x[NK];
+#pragma unroll
+        for (int kk = 0; kk < NK; ++kk) x[kk] = tin[io + koff[kk]];
+        if constexpr (NN == 1) {
+            float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int kk = 0; kk < NK; ++kk) cfma(acc, x[kk], Bm[kk]);
+            tout[oo + S.noff[0]] = acc;
+        } else {
+            // two outputs per iteration; B[kappa][nu], B[kappa][nu+1] in one 16-byte load
+#pragma unroll 1
+            for (int nn = 0; nn < NN; nn += 2) {
+                float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int kk = 0; kk < NK; ++kk) {
+                    const float4 b = *reinterpret_cast<const float4 *>(Bm + kk * NN + nn);
+                    cfma(a0, x[kk], make_float2(b.x, b.y));
+                    cfma(a1, x[kk], make_float2(b.z, b.w));
+                }
+                tout[oo + S.noff[nn]] = a0;
+                tout[oo + S.noff[nn + 1]] = a1;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void copy_body(const float2 *__restrict__ tin, float2 *__restrict__ tout,
+                                          const DevStep &S, int nt) {
+    const int nrest = 1 << S.rest;
+    for (int r = threadIdx.x; r < nrest; r += nt) {
+        const int io = S.in_lo[r & 63] + S.in_hi[r >> 6];
+        const int oo = S.out_lo[r & 63] + S.out_hi[r >> 6];
+        tout[oo] = tin[io];
+    }
+}
+
+__device__ void run_step(const float2 *tin, float2 *tout, const DevStep &S, const float2 *Bm,
+                         int nt) {
+    if (S.branch < 0) {
+        copy_body(tin, tout, S, nt);
+        return;
+    }
+    switch (S.k * 8 + S.n) {
+#define TN_CASE(K, N) \
+    case K * 8 + N: step_body<K, N>(tin, tout, S, Bm, nt); break;
+        TN_CASE(1, 0) TN_CASE(1, 1) TN_CASE(1, 2) TN_CASE(1, 3) TN_CASE(1, 4)
+        TN_CASE(2, 0) TN_CASE(2, 1) TN_CASE(2, 2) TN_CASE(2, 3) TN_CASE(2, 4)
+        TN_CASE(3, 0) TN_CASE(3, 1) TN_CASE(3, 2) TN_CASE(3, 3) TN_CASE(3, 4)
+        TN_CASE(4, 0) TN_CASE(4, 1) TN_CASE(4, 2) TN_CASE(4, 3) TN_CASE(4, 4)
+#undef TN_CASE
+        default: break;
+    }
+}
+
+constexpr int PASS_THREADS = 256;
+
+
+__global__ void __launch_bounds__(PASS_THREADS)
+pass_kernel(const DevPass *__restrict__ gpass, const int *__restrict__ chunks,
+            const DevBranch *__restrict__ branches, const float2 *__restrict__ pool,
+            const float2 *__restrict__ in, float2 *__restrict__ out, BatchArgs ba) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    DevPass &P = *reinterpret_cast<DevPass *>(smem);
+    {
+        const int4 *src = reinterpret_cast<const int4 *>(gpass);
+        int4 *dst = reinterpret_cast<int4 *>(smem);
+        for (int i = threadIdx.x; i < (int)(sizeof(DevPass) / 16); i += PASS_THREADS) dst[i] = src[i];
+    }
+    __syncthreads();
+    constexpr size_t PASS_BYTES = (sizeof(DevPass) + 15) / 16 * 16;
+    float2 *tA = reinterpret_cast<float2 *>(smem + PASS_BYTES);
+    float2 *tB = tA + P.tile_max;
+    float2 *bm = tB + P.tile_max;
+    // branch matrices of the pass's steps sit back to back after the tiles
+    auto bm_off = [&](int t) {
+        int o = 0;
+        for (int u = 0; u < t; ++u)
+            if (P.steps[u].branch >= 0) o += 1 << (P.steps[u].k + P.steps[u].n);
+        return o;
+    };
+    const int64_t n_units = (int64_t)ba.n_items * P.n_tiles;
+    const int64_t base = ba.state->slice_base;
+    const int64_t send = ba.state->slice_end;
+    const int tin_n = 1 << P.t_in, tout_n = 1 << P.t_out;
+    const int cin_mask = (1 << P.c_in) - 1, cout_mask = (1 << P.c_out) - 1;
+    const int *cin_tab = chunks + P.chunk_in_base;
+    const int *cout_tab = chunks + P.chunk_out_base;
+    int64_t last_item = -1;
+    for (int64_t u = blockIdx.x; u < n_units; u += gridDim.x) {
+        const int64_t item = u >> P.n_free;
+        const int64_t tile = u & (P.n_tiles - 1);
+        const int pl = (int)(item / ba.SB);
+        const int p = ba.p0 + pl;
+        const int64_t s = base + (item - (int64_t)pl * ba.SB);
+        if (s >= send) continue;  // uniform over the block
+        if (item != last_item) {
+            for (int t = 0; t < P.n_steps; ++t) {
+                const int br = P.steps[t].branch;
+                if (br < 0) continue;
+                const DevBranch &b = branches[br];
+                const float2 *src = pool + branch_offset(b, p, s);
+                const int cnt = 1 << (P.steps[t].k + P.steps[t].n);
+                const int bo = bm_off(t);
+                for (int i = threadIdx.x; i < cnt; i += PASS_THREADS) bm[bo + i] = src[i];
+            }
+            last_item = item;
+        }
+        int64_t ib = 0, ob = 0;
+        for (int f = 0; f < P.n_free; ++f)
+            if ((tile >> f) & 1) {
+                ib += P.free_in[f];
+                ob += P.free_out[f];
+            }
+        const float2 *src;
+        if (P.in_branch >= 0)
+            src = pool + branch_offset(branches[P.in_branch], p, s);
+        else
+            src = in + item * P.in_item_stride;
+        float2 *dst = out + item * P.out_item_stride;
+        // load tile: tile-local index = chunk * 2^c_in + w
+        if (P.c_in >= 1) {
+            for (int idx = threadIdx.x * 2; idx < tin_n; idx += PASS_THREADS * 2) {
+                const int j = idx >> P.c_in, w = idx & cin_mask;
+                const float4 v = *reinterpret_cast<const float4 *>(src + ib + cin_tab[j] + w);
+                *reinterpret_cast<float4 *>(tA + idx) = v;
+            }
+        } else {
+            for (int idx = threadIdx.x; idx < tin_n; idx += PASS_THREADS)
+                tA[idx] = src[ib + cin_tab[idx]];
+        }
+        __syncthreads();
+        float2 *cur = tA, *nxt = tB;
+        for (int t = 0; t < P.n_steps; ++t) {
+            run_step(cur, nxt, P.steps[t], bm + bm_off(t), PASS_THREADS);
+            __syncthreads();
+            float2 *tmp = cur;
+            cur = nxt;
+            nxt = tmp;
+        }
+        if (P.c_out >= 1) {
+            for (int idx = threadIdx.x * 2; idx < tout_n; idx += PASS_THREADS * 2) {
+                const int j = idx >> P.c_out, w = idx & cout_mask;
+                *reinterpret_cast<float4 *>(dst + ob + cout_tab[j] + w) =
+                    *reinterpret_cast<const float4 *>(cur + idx);
+            }
+        } else {
+            for (int idx = threadIdx.x; idx < tout_n; idx += PASS_THREADS)
+                dst[ob + cout_tab[idx]] = cur[idx];
+        }
+        __syncthreads();
+    }
+}
+
+static size_t pass_smem_bytes(const DevPass &P) {
+    size_t b = (sizeof(DevPass) + 15) / 16 * 16;
+    b += 2 * (size_t)P.tile_max * sizeof(float2);
+    for (int t = 0; t < P.n_steps; ++t)
+        if (P.steps[t].branch >= 0) b += ((size_t)1 << (P.steps[t].k + P.steps[t].n)) * sizeof(float2);
+    return b;
+}
+
+cudaError_t launch_pass(const DevPass *d_pass, const DevPass &h_pass, const int *d_chunks,
+                        const DevBranch *d_branches, const DevBranch *h_branches,
+                        const float2 *pool, const float2 *in, float2 *out, BatchArgs ba,
+                        cudaStream_t st) {
+    (void)h_branches;
+    static int num_sms = 0;
+    if (!num_sms) {
+        int dev;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    const size_t smem = pass_smem_bytes(h_pass);
+    int occ = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pass_kernel, PASS_THREADS, smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    const int64_t units = (int64_t)ba.n_items * h_pass.n_tiles;
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(units, (int64_t)num_sms * occ));
+    pass_kernel<<<(unsigned)grid, PASS_THREADS, smem, st>>>(d_pass, d_chunks, d_branches, pool, in,
+                                                            out, ba);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------- small contraction
+// Branch pre-computation (Supp. A.3): one pairwise step on small tensors,
+// C[o] = sum_c A[ia(o) + ja(c)] * B[ib(o) + jb(c)]; B == nullptr means a
+// permutation of A.
+__global__ void small_contract_kernel(const float2 *__restrict__ A, const float2 *__restrict__ B,
+                                      float2 *__restrict__ C, SmallContract d) {
+    const int64_t nout = (int64_t)1 << d.rc;
+    const int64_t nsum = (int64_t)1 << d.k;
+    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < nout;
+         o += (int64_t)gridDim.x * blockDim.x) {
+        int64_t ia = 0, ib = 0;
+        for (int j = 0; j < d.rc; ++j) {
+            if (!((o >> j) & 1)) continue;
+            if (d.a_out[j] >= 0)
+                ia += (int64_t)1 << d.a_out[j];
+            else
+                ib += (int64_t)1 << d.b_out[j];
+        }
+        if (!B) {
+            C[o] = A[ia];
+            continue;
+        }
+        float2 acc = make_float2(0.f, 0.f);
+        for (int64_t c = 0; c < nsum; ++c) {
+            int64_t ja = ia, jb = ib;
+            for (int t = 0; t < d.k; ++t)
+                if ((c >> t) & 1) {
+                    ja += (int64_t)1 << d.a_k[t];
+                    jb += (int64_t)1 << d.b_k[t];
+                }
+            cfma(acc, A[ja], B[jb]);
+        }
+        C[o] = acc;
+    }
+}
+
+cudaError_t launch_small_contract(const float2 *A, const float2 *B, float2 *C,
+                                  const SmallContract &d, cudaStream_t st) {
+    const int64_t nout = (int64_t)1 << d.rc;
+    const int threads = 256;
+    const int64_t blocks = std::min<int64_t>((nout + threads - 1) / threads, 4096);
+    small_contract_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), threads, 0, st>>>(A, B, C, d);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- SIMT GEMM
+// C[m][nu] = sum_kappa A[m][kappa] * B[kappa][nu] for one batch item per
+// blockIdx.z. A block computes a BM x BN tile (BN = min(N, 256), BM =
+// min(4096 / BN, 512)), staging 8-wide slabs of A and B in shared memory;
+// thread t owns outputs t + 256 i.
+constexpr int G_THREADS = 256;
+constexpr int G_BK = 8;
+
+struct GemmItemSrc {
+    // A / C base per item: base + item * stride; B per item from the branch
+    // table (stem steps) or base + item * strideB (plain GEMM).
+    const float2 *A;
+    float2 *C;
+    const float2 *B;
+    int64_t sA, sB, sC;
+    const DevBranch *br;  // non-null: B from branch storage
+    const float2 *pool;
+    BatchArgs ba;
+    int use_batch;        // 1: items follow BatchArgs (slices/prefixes)
+};
+
+__global__ void __launch_bounds__(G_THREADS)
+cgemm_simt_kernel(GemmItemSrc g, int64_t M, int K, int N, int BM, int BN) {
+    extern __shared__ __align__(16) float2 gsm[];
+    float2 *As = gsm;                      // BM x (BK + 1)
+    float2 *Bs = gsm + BM * (G_BK + 1);    // BK x BN
+    const int64_t item = blockIdx.z;
+    const float2 *A = g.A + item * g.sA;
+    float2 *C = g.C + item * g.sC;
+    const float2 *B;
+    if (g.use_batch) {
+        const int pl = (int)(item / g.ba.SB);
+        const int64_t s = g.ba.state->slice_base + (item - (int64_t)pl * g.ba.SB);
+        if (s >= g.ba.state->slice_end) return;
+        B = g.br ? g.pool + branch_offset(*g.br, g.ba.p0 + pl, s) : g.B + item * g.sB;
+    } else {
+        B = g.B + item * g.sB;
+    }
+    const int64_t m0 = (int64_t)blockIdx.x * BM;
+    const int n0 = blockIdx.y * BN;
+    const int nout = BM * BN;
+    float2 acc[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) acc[i] = make_float2(0.f, 0.f);
+    for (int k0 = 0; k0 < K; k0 += G_BK) {
+        const int bk = min(G_BK, K - k0);
+        for (int i = threadIdx.x; i < BM * bk; i += G_THREADS) {
+            const int r = i / bk, c = i % bk;
+            const int64_t m = m0 + r;
+            As[r * (G_BK + 1) + c] = (m < M) ? A[m * K + k0 + c] : make_float2(0.f, 0.f);
+        }
+        for (int i = threadIdx.x; i < bk * BN; i += G_THREADS) {
+            const int r = i / BN, c = i % BN;
+            Bs[r * BN + c] = (n0 + c < N) ? B[(int64_t)(k0 + r) * N + n0 + c] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int o = threadIdx.x + i * G_THREADS;
+            if (o < nout) {
+                const int r = o / BN, c = o % BN;
+                float2 a = acc[i];
+                for (int kk = 0; kk < bk; ++kk) cfma(a, As[r * (G_BK + 1) + kk], Bs[kk * BN + c]);
+                acc[i] = a;
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const int o = threadIdx.x + i * G_THREADS;
+        if (o < nout) {
+            const int r = o / BN, c = o % BN;
+            const int64_t m = m0 + r;
+            if (m < M && n0 + c < N) C[m * N + n0 + c] = acc[i];
+        }
+    }
+}
+
+static cudaError_t run_simt_gemm(const GemmItemSrc &g, int64_t M, int64_t K, int64_t N,
+                                 int64_t batch, cudaStream_t st) {
+    if (K <= 0 || N <= 0 || M <= 0 || batch <= 0) return cudaSuccess;
+    if (batch > 65535) return cudaErrorInvalidValue;
+    const int BN = (int)std::min<int64_t>(N, 256);
+    const int BM = std::min(4096 / BN, 512);
+    const int64_t gx = (M + BM - 1) / BM;
+    const int64_t gy = (N + BN - 1) / BN;
+    if (gx > 0x7fffffffLL || gy > 65535) return cudaErrorInvalidValue;
+    const size_t smem = ((size_t)BM * (G_BK + 1) + (size_t)G_BK * BN) * sizeof(float2);
+    dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)batch);
+    cgemm_simt_kernel<<<grid, G_THREADS, smem, st>>>(g, M, (int)K, (int)N, BM, BN);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stem_gemm(const float2 *A, float2 *C, int64_t M, int k, int n, int64_t strideA,
+                             int64_t strideC, const DevBranch *d_branch_entry, const float2 *pool,
+                             BatchArgs ba, tn_precision prec, cudaStream_t st) {
+    if (prec != TN_PREC_FP32_SIMT) {
+        if (!tc_gemm_supported(k, n)) return cudaErrorNotSupported;
+        return launch_tc_stem_gemm(A, C, M, k, n, strideA, strideC, d_branch_entry, pool, ba, prec, st);
+    }
+    GemmItemSrc g{A, C, nullptr, strideA, 0, strideC, d_branch_entry, pool, ba, 1};
+    return run_simt_gemm(g, M, (int64_t)1 << k, (int64_t)1 << n, ba.n_items, st);
+}
+
+cudaError_t launch_cgemm(const float2 *A, const float2 *B, float2 *C, int64_t M, int64_t K,
+                         int64_t N, int64_t batch, int64_t sA, int64_t sB, int64_t sC,
+                         tn_precision prec, cudaStream_t st) {
+    (void)prec;
+    GemmItemSrc g{A, C, B, sA, sB, sC, nullptr, nullptr, BatchArgs{nullptr, 1, 0, 0}, 0};
+    return run_simt_gemm(g, M, K, N, batch, st);
+}
+
+// ---------------------------------------------------- slice sum (FP64)
+// Neumaier-compensated running sum, per component.
+__device__ __forceinline__ void neumaier(double &sum, double &comp, double v) {
+    const double t = sum + v;
+    if (fabs(sum) >= fabs(v))
+        comp += (sum - t) + v;
+    else
+        comp += (v - t) + sum;
+    sum = t;
+}
+
+// One thread per (prefix, open index): adds the batch's slices in slice order.
+__global__ void accumulate_kernel(const float2 *__restrict__ fin, int n_open,
+                                  const int *__restrict__ pos, double2 *sum, double2 *comp,
+                                  BatchArgs ba, int n_prefix_launch, int total_prefix_stride) {
+    const int nb = 1 << n_open;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= n_prefix_launch * nb) return;
+    const int pl = tid / nb, o = tid % nb;
+    int idx = 0;
+    for (int i = 0; i < n_open; ++i)
+        if ((o >> (n_open - 1 - i)) & 1) idx += 1 << pos[i];
+    const int64_t base = ba.state->slice_base, send = ba.state->slice_end;
+    const int64_t gi = (int64_t)(ba.p0 + pl) * nb + o;
+    (void)total_prefix_stride;
+    double sr = sum[gi].x, si = sum[gi].y, cr = comp[gi].x, ci = comp[gi].y;
+    for (int j = 0; j < ba.SB; ++j) {
+        if (base + j >= send) break;
+        const float2 v = fin[((int64_t)pl * ba.SB + j) * nb + idx];
+        neumaier(sr, cr, (double)v.x);
+        neumaier(si, ci, (double)v.y);
+    }
+    sum[gi] = make_double2(sr, si);
+    comp[gi] = make_double2(cr, ci);
+}
+
+cudaError_t launch_accumulate(const float2 *fin, int n_open, const int *d_pos, double2 *sum,
+                              double2 *comp, BatchArgs ba, int n_prefix_launch, cudaStream_t st) {
+    const int n = n_prefix_launch << n_open;
+    accumulate_kernel<<<(n + 127) / 128, 128, 0, st>>>(fin, n_open, d_pos, sum, comp, ba,
+                                                       n_prefix_launch, 0);
+    return cudaGetLastError();
+}
+
+__global__ void advance_kernel(DevState *s, int64_t by) { s->slice_base += by; }
+
+cudaError_t launch_advance(DevState *state, int64_t by, cudaStream_t st) {
+    advance_kernel<<<1, 1, 0, st>>>(state, by);
+    return cudaGetLastError();
+}
+
+__global__ void finalize_kernel(const double2 *sum, const double2 *comp, double2 *out, int64_t n,
+                                int accumulate) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double2 v = make_double2(sum[i].x + comp[i].x, sum[i].y + comp[i].y);
+    if (accumulate) {
+        v.x += out[i].x;
+        v.y += out[i].y;
+    }
+    out[i] = v;
+}
+
+cudaError_t launch_finalize(const double2 *sum, const double2 *comp, double2 *out, int64_t n,
+                            int accumulate, cudaStream_t st) {
+    finalize_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(sum, comp, out, n, accumulate);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ XEB
+// Sum of |amp|^2 in FP64: block tree reduction, then one compensated pass
+// over the block partials by a single thread (deterministic order).
+__global__ void xeb_partial_kernel(const double2 *__restrict__ a, int64_t n, double *part) {
+    __shared__ double sh[256];
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        acc += a[i].x * a[i].x + a[i].y * a[i].y;
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void xeb_final_kernel(const double *part, int nb, double *out) {
+    double s = 0.0, c = 0.0;
+    for (int i = 0; i < nb; ++i) neumaier(s, c, part[i]);
+    *out = s + c;
+}
+
+cudaError_t launch_xeb_sum(const double2 *amps, int64_t n, double *out_sum, cudaStream_t st) {
+    // out_sum must have room for 1 + 256 doubles: [result, partials...]
+    const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(256, (n + 255) / 256));
+    xeb_partial_kernel<<<nb, 256, 0, st>>>(amps, n, out_sum + 1);
+    xeb_final_kernel<<<1, 1, 0, st>>>(out_sum + 1, nb, out_sum);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------- permute
+// Input bit j -> output bit perm[j]; read coalesced, write through a
+// per-byte lookup of the destination offset.
+__global__ void permute_kernel(const float2 *__restrict__ in, float2 *__restrict__ out, int rank,
+                               const int *__restrict__ tab) {
+    const int64_t n = (int64_t)1 << rank;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t o = 0;
+        for (int b = 0; b < 4; ++b) o += (int64_t)(unsigned)tab[b * 256 + ((i >> (8 * b)) & 255)];
+        out[o] = in[i];
+    }
+}
+
+cudaError_t launch_permute(const float2 *in, float2 *out, int rank, const int *d_tab,
+                           cudaStream_t st) {
+    const int64_t n = (int64_t)1 << rank;
+    const int threads = 256;
+    const int64_t blocks = std::min<int64_t>((n + threads - 1) / threads, 152 * 16);
+    permute_kernel<<<(unsigned)blocks, threads, 0, st>>>(in, out, rank, d_tab);
+    return cudaGetLastError();
+}
+
+// Raise the dynamic shared-memory limits once, outside any stream capture.
+cudaError_t init_kernels() {
+    cudaError_t e = cudaFuncSetAttribute(pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         200 * 1024);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(cgemm_simt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                96 * 1024);
+}
+
+}  // namespace tn

@@ -1,0 +1,69 @@
+// Host-side launchers of the CUDA kernels (kernels.cu, gemm_tc.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace tn {
+
+// Per-launch batch bookkeeping kept in device memory, so that a captured
+// graph can be replayed for successive slice batches.
+struct DevState {
+    int64_t slice_base;  // slice of batch item 0
+    int64_t slice_end;   // end of the requested slice range
+    int32_t err;         // nonzero: a kernel met an out-of-range descriptor
+    int32_t pad;
+};
+
+// Batch items: item = p_local * SB + j -> prefix p0 + p_local, slice base + j.
+struct BatchArgs {
+    const DevState *state;
+    int SB;          // slices per batch
+    int n_items;     // items in this launch
+    int p0;          // first prefix of this launch
+};
+
+struct SmallContract {
+    int ra, rb, rc, k;
+    int a_out[40], b_out[40];  // per output bit: position in A / B, -1 if absent
+    int a_k[40], b_k[40];      // per contracted bit: position in A / B
+};
+
+cudaError_t init_kernels();
+cudaError_t launch_pass(const DevPass *d_pass, const DevPass &h_pass, const int *d_chunks,
+                        const DevBranch *d_branches, const DevBranch *h_branches,
+                        const float2 *pool, const float2 *in, float2 *out, BatchArgs ba,
+                        cudaStream_t st);
+
+cudaError_t launch_small_contract(const float2 *A, const float2 *B, float2 *C,
+                                  const SmallContract &d, cudaStream_t st);
+
+// Stem GEMM step over batch items: C_item[m][nu] = sum_kappa A_item[m][kappa] *
+// Branch_item[kappa][nu]; A item stride 2^r_in, C item stride 2^r_out.
+cudaError_t launch_stem_gemm(const float2 *A, float2 *C, int64_t M, int k, int n, int64_t strideA,
+                             int64_t strideC, const DevBranch *d_branch_entry, const float2 *pool,
+                             BatchArgs ba, tn_precision prec, cudaStream_t st);
+
+// Plain batched complex GEMM (tn_cgemm).
+cudaError_t launch_cgemm(const float2 *A, const float2 *B, float2 *C, int64_t M, int64_t K,
+                         int64_t N, int64_t batch, int64_t sA, int64_t sB, int64_t sC,
+                         tn_precision prec, cudaStream_t st);
+
+// FP64 Neumaier accumulation of final open tensors into sum / comp.
+cudaError_t launch_accumulate(const float2 *fin, int n_open, const int *d_pos, double2 *sum,
+                              double2 *comp, BatchArgs ba, int n_prefix_total, cudaStream_t st);
+cudaError_t launch_advance(DevState *state, int64_t by, cudaStream_t st);
+cudaError_t launch_finalize(const double2 *sum, const double2 *comp, double2 *out, int64_t n,
+                            int accumulate, cudaStream_t st);
+cudaError_t launch_xeb_sum(const double2 *amps, int64_t n, double *out_sum, cudaStream_t st);
+cudaError_t launch_permute(const float2 *in, float2 *out, int rank, const int *perm,
+                           cudaStream_t st);
+
+bool tc_gemm_supported(int k, int n);
+cudaError_t launch_tc_stem_gemm(const float2 *A, float2 *C, int64_t M, int k, int n,
+                                int64_t strideA, int64_t strideC, const DevBranch *d_branch_entry,
+                                const float2 *pool, BatchArgs ba, tn_precision prec,
+                                cudaStream_t st);
+
+}  // namespace tn

@@ -1,0 +1,528 @@
+// Turn a scheme (stem order + branches + sliced edges) into what the kernels
+// run: bit layouts of every stem tensor and branch, the fused HBM passes, and
+// the plain permute + GEMM steps.
+//
+// A stem tensor of rank r is 2^r complex64 values; its layout lists the edge
+// held by each bit of the linear index (bit 0 = contiguous). A fused pass
+// reads tiles made of 2^c-entry contiguous chunks, applies several stem steps
+// to each tile in shared memory and writes the tile in the next layout, so a
+// run of steps costs one read and one write of the stem tensor.
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <set>
+
+#include "internal.h"
+#include "plan.h"
+
+namespace tn {
+
+namespace {
+
+struct StepSets {
+    std::vector<int> K, N;  // branch kappa / nu edges, ascending
+    int r_in, r_out;
+};
+
+int pos_of(const std::vector<int> &layout, int e) {
+    for (size_t i = 0; i < layout.size(); ++i)
+        if (layout[i] == e) return (int)i;
+    return -1;
+}
+
+// Order edges by the index of the step that next contracts them (soonest
+// first; never = last), ties by edge id.
+std::vector<int> sort_by_next_use(std::vector<int> edges, const std::vector<StepSets> &steps,
+                                  int from) {
+    std::map<int, int> use;
+    for (int e : edges) use[e] = 1 << 30;
+    for (int i = (int)steps.size() - 1; i >= from; --i)
+        for (int e : steps[(size_t)i].K)
+            if (use.count(e)) use[e] = i;
+    std::sort(edges.begin(), edges.end(), [&](int a, int b) {
+        if (use[a] != use[b]) return use[a] < use[b];
+        return a < b;
+    });
+    return edges;
+}
+
+void fill_tables(DevStep &st, const std::vector<int> &lam_in, const std::vector<int> &lam_out,
+                 const std::vector<int> &K, const std::vector<int> &N) {
+    std::vector<int> rest;
+    for (int e : lam_in)
+        if (std::find(K.begin(), K.end(), e) == K.end()) rest.push_back(e);
+    st.k = (int)K.size();
+    st.n = (int)N.size();
+    st.rest = (int)rest.size();
+    if (st.rest > 12) fail(TN_ERR_UNSUPPORTED, "internal: tile rest exceeds 12 bits");
+    for (int kk = 0; kk < 16; ++kk) {
+        int o = 0;
+        for (int b = 0; b < st.k; ++b)
+            if ((kk >> b) & 1) o += 1 << pos_of(lam_in, K[(size_t)b]);
+        st.koff[kk] = (kk < (1 << st.k)) ? o : 0;
+    }
+    for (int nn = 0; nn < 16; ++nn) {
+        int o = 0;
+        for (int b = 0; b < st.n; ++b)
+            if ((nn >> b) & 1) o += 1 << pos_of(lam_out, N[(size_t)b]);
+        st.noff[nn] = (nn < (1 << st.n)) ? o : 0;
+    }
+    for (int half = 0; half < 2; ++half) {
+        for (int v = 0; v < 64; ++v) {
+            int oi = 0, oo = 0;
+            for (int b = 0; b < 6; ++b) {
+                int rb = half * 6 + b;
+                if (rb >= st.rest || !((v >> b) & 1)) continue;
+                int pi = pos_of(lam_in, rest[(size_t)rb]);
+                int po = pos_of(lam_out, rest[(size_t)rb]);
+                if (pi < 0 || po < 0) fail(TN_ERR_UNSUPPORTED, "internal: rest edge lost");
+                oi += 1 << pi;
+                oo += 1 << po;
+            }
+            if (half == 0) {
+                st.in_lo[v] = oi;
+                st.out_lo[v] = oo;
+            } else {
+                st.in_hi[v] = oi;
+                st.out_hi[v] = oo;
+            }
+        }
+    }
+}
+
+// Build a pass from in-layout to out-layout applying `group` steps (indices
+// into steps, with branch ids br). tile_in_edges must contain the low c_in
+// input edges and every input edge the group contracts.
+DevPass build_pass(const std::vector<int> &Lin, const std::vector<int> &Lout, int c_in, int c_out,
+                   const std::set<int> &tile_in_edges, const std::vector<int> &group,
+                   const std::vector<StepSets> &steps, const std::vector<int> &branch_of_step,
+                   std::vector<int> &chunk_table) {
+    DevPass P{};
+    P.r_in = (int)Lin.size();
+    P.r_out = (int)Lout.size();
+    P.c_in = c_in;
+    P.c_out = c_out;
+    P.in_branch = -1;
+    // tile-local input layout: tile edges by ascending input position
+    std::vector<int> lam_in;
+    for (int e : Lin)
+        if (tile_in_edges.count(e)) lam_in.push_back(e);
+    P.t_in = (int)lam_in.size();
+    // evolve the tile through the group
+    std::vector<std::vector<int>> lams{lam_in};
+    std::vector<int> cur = lam_in;
+    for (int s : group) {
+        std::vector<int> nxt;
+        for (int e : cur)
+            if (std::find(steps[(size_t)s].K.begin(), steps[(size_t)s].K.end(), e) ==
+                steps[(size_t)s].K.end())
+                nxt.push_back(e);
+        for (int e : steps[(size_t)s].N) nxt.push_back(e);
+        lams.push_back(nxt);
+        cur = nxt;
+    }
+    std::set<int> tile_out_set(cur.begin(), cur.end());
+    // tile-local output layout: tile-out edges by ascending output position
+    std::vector<int> lam_out;
+    for (int e : Lout)
+        if (tile_out_set.count(e)) lam_out.push_back(e);
+    if (lam_out.size() != cur.size()) fail(TN_ERR_UNSUPPORTED, "internal: tile-out mismatch");
+    P.t_out = (int)lam_out.size();
+    lams.back() = lam_out;
+    P.tile_max = 0;
+    for (auto &l : lams) P.tile_max = std::max(P.tile_max, 1 << (int)l.size());
+    // low c_in input positions must be tile edges; low c_out output positions too
+    for (int p = 0; p < c_in; ++p)
+        if (!tile_in_edges.count(Lin[(size_t)p])) fail(TN_ERR_UNSUPPORTED, "internal: c_in");
+    for (int p = 0; p < c_out; ++p)
+        if (!tile_out_set.count(Lout[(size_t)p])) fail(TN_ERR_UNSUPPORTED, "internal: c_out");
+    // free edges
+    P.n_free = 0;
+    for (int e : Lin) {
+        if (tile_in_edges.count(e)) continue;
+        int po = pos_of(Lout, e);
+        if (po < 0) fail(TN_ERR_UNSUPPORTED, "internal: free edge missing from output");
+        if (P.n_free >= MAX_FREE) fail(TN_ERR_UNSUPPORTED, "too many free bits");
+        P.free_in[P.n_free] = 1ll << pos_of(Lin, e);
+        P.free_out[P.n_free] = 1ll << po;
+        P.n_free++;
+    }
+    if (P.r_out - P.t_out != P.n_free) fail(TN_ERR_UNSUPPORTED, "internal: free count");
+    P.n_tiles = 1ll << P.n_free;
+    // chunk tables
+    P.chunk_in_base = (int)chunk_table.size();
+    for (int j = 0; j < (1 << (P.t_in - c_in)); ++j) {
+        int o = 0;
+        for (int b = 0; b < P.t_in - c_in; ++b)
+            if ((j >> b) & 1) o += 1 << pos_of(Lin, lam_in[(size_t)(c_in + b)]);
+        chunk_table.push_back(o);
+    }
+    P.chunk_out_base = (int)chunk_table.size();
+    for (int j = 0; j < (1 << (P.t_out - c_out)); ++j) {
+        int o = 0;
+        for (int b = 0; b < P.t_out - c_out; ++b)
+            if ((j >> b) & 1) o += 1 << pos_of(Lout, lam_out[(size_t)(c_out + b)]);
+        chunk_table.push_back(o);
+    }
+    // steps
+    if (group.empty()) {
+        P.n_steps = 1;
+        fill_tables(P.steps[0], lam_in, lam_out, {}, {});
+        P.steps[0].branch = -1;
+    } else {
+        P.n_steps = (int)group.size();
+        for (size_t t = 0; t < group.size(); ++t) {
+            int s = group[t];
+            fill_tables(P.steps[t], lams[t], lams[t + 1], steps[(size_t)s].K, steps[(size_t)s].N);
+            P.steps[t].branch = branch_of_step[(size_t)s];
+        }
+    }
+    P.in_item_stride = 1ll << P.r_in;
+    P.out_item_stride = 1ll << P.r_out;
+    return P;
+}
+
+// Check that a pass's descriptors address exactly the tensors they claim:
+// the input (output) bit positions used by chunks, chunk tables and free
+// bits partition [0, r_in) ([0, r_out)), and every tile offset of every step
+// partitions the tile state it reads or writes. Any violation would index
+// outside a buffer, so it is rejected here on the host.
+void validate_pass(const DevPass &P, const std::vector<int> &chunks) {
+    auto bad = [](const char *what) { fail(TN_ERR_UNSUPPORTED, std::string("internal: pass ") + what); };
+    if (P.r_in < 0 || P.r_in > 31 || P.r_out < 0 || P.r_out > 31) bad("rank");
+    if (P.t_in > MAX_TILE_BITS + 1 || P.t_out > MAX_TILE_BITS + 1) bad("tile bits");
+    if (P.c_in > P.t_in || P.c_out > P.t_out) bad("chunk bits");
+    if (P.n_steps < 1 || P.n_steps > MAX_PASS_STEPS) bad("step count");
+    auto check_side = [&](int r, int t, int c, int base, const int64_t *free) {
+        uint64_t mask = (c > 0) ? ((1ull << c) - 1) : 0;
+        int bits = c;
+        for (int b = 0; b < t - c; ++b) {
+            int v = chunks[(size_t)base + (1u << b)];
+            if (v <= 0 || (v & (v - 1))) bad("chunk table entry");
+            if (mask & (uint64_t)v) bad("chunk overlap");
+            mask |= (uint64_t)v;
+            ++bits;
+        }
+        for (int f = 0; f < P.n_free; ++f) {
+            uint64_t v = (uint64_t)free[f];
+            if (!v || (v & (v - 1))) bad("free stride");
+            if (mask & v) bad("free overlap");
+            mask |= v;
+            ++bits;
+        }
+        if (bits != r || mask != ((r == 64) ? ~0ull : ((1ull << r) - 1))) bad("index partition");
+        // chunk table entries are sums of the single-bit entries
+        for (int j = 0; j < (1 << (t - c)); ++j) {
+            int o = 0;
+            for (int b = 0; b < t - c; ++b)
+                if ((j >> b) & 1) o += chunks[(size_t)base + (1u << b)];
+            if (chunks[(size_t)base + (size_t)j] != o) bad("chunk table sum");
+        }
+    };
+    check_side(P.r_in, P.t_in, P.c_in, P.chunk_in_base, P.free_in);
+    check_side(P.r_out, P.t_out, P.c_out, P.chunk_out_base, P.free_out);
+    int t = P.t_in;
+    for (int i = 0; i < P.n_steps; ++i) {
+        const DevStep &S = P.steps[i];
+        if (S.k < 0 || S.k > MAX_STEP_K || S.n < 0 || S.n > MAX_STEP_K) bad("step k/n");
+        if (S.branch < 0 && (S.k || S.n)) bad("copy step with k/n");
+        if (S.rest != t - S.k || S.rest > 12) bad("rest bits");
+        const int t2 = S.rest + S.n;
+        if ((1 << t) > P.tile_max || (1 << t2) > P.tile_max) bad("tile size");
+        uint64_t mi = 0, mo = 0;
+        for (int b = 0; b < S.rest; ++b) {
+            int vi = b < 6 ? S.in_lo[1 << b] : S.in_hi[1 << (b - 6)];
+            int vo = b < 6 ? S.out_lo[1 << b] : S.out_hi[1 << (b - 6)];
+            if (vi <= 0 || (vi & (vi - 1)) || (mi & (uint64_t)vi)) bad("rest in offset");
+            if (vo <= 0 || (vo & (vo - 1)) || (mo & (uint64_t)vo)) bad("rest out offset");
+            mi |= (uint64_t)vi;
+            mo |= (uint64_t)vo;
+        }
+        for (int b = 0; b < S.k; ++b) {
+            int v = S.koff[1 << b];
+            if (v <= 0 || (v & (v - 1)) || (mi & (uint64_t)v)) bad("kappa offset");
+            mi |= (uint64_t)v;
+        }
+        for (int b = 0; b < S.n; ++b) {
+            int v = S.noff[1 << b];
+            if (v <= 0 || (v & (v - 1)) || (mo & (uint64_t)v)) bad("nu offset");
+            mo |= (uint64_t)v;
+        }
+        if (mi != (1ull << t) - 1 || mo != (1ull << t2) - 1) bad("tile partition");
+        t = t2;
+    }
+    if (t != P.t_out) bad("final tile bits");
+    if (P.n_tiles != (1ll << P.n_free)) bad("tile count");
+}
+
+}  // namespace
+
+BuiltStem build_stem_plan(const Network &net, const Scheme &s, const tn_plan_opts &o) {
+    BuiltStem R;
+    const int T_MAX = (o.tile_bits > 0) ? std::min(o.tile_bits, MAX_TILE_BITS) : 11;
+    const int C_BITS = 4;
+    const int max_steps = (o.max_pass_steps > 0) ? std::min(o.max_pass_steps, MAX_PASS_STEPS) : 6;
+    const int gemm_min = (o.gemm_min_kn > 0) ? o.gemm_min_kn : 5;
+    const Bits &sl = s.sliced;
+    std::vector<Bits> B;
+    for (auto &c : s.clusters) B.push_back(c.out.andnot(sl));
+    const int L = (int)s.stem_order.size();
+
+    // step sets
+    std::vector<StepSets> steps((size_t)L);
+    Bits S = B[(size_t)s.seed_cluster];
+    int maxr = S.count();
+    for (int i = 0; i < L; ++i) {
+        const Bits &b = B[(size_t)s.stem_order[(size_t)i]];
+        steps[(size_t)i].K = (S & b).list();
+        steps[(size_t)i].N = b.andnot(S).list();
+        steps[(size_t)i].r_in = S.count();
+        S ^= b;
+        steps[(size_t)i].r_out = S.count();
+        maxr = std::max(maxr, S.count());
+    }
+    std::vector<int> final_edges = S.list();
+    {
+        std::vector<int> oe(net.open_edges.begin(), net.open_edges.end());
+        std::sort(oe.begin(), oe.end());
+        if (final_edges != oe) fail(TN_ERR_INVALID_ARG, "scheme does not end on the open edges");
+    }
+    if (maxr > 31) fail(TN_ERR_UNSUPPORTED, "stem tensors above 2^31 entries are not supported");
+    R.sp.max_rank = maxr;
+
+    // branch layouts
+    R.layouts.resize(s.clusters.size());
+    std::vector<int> branch_of_step((size_t)L);
+    for (int i = 0; i < L; ++i) {
+        int c = s.stem_order[(size_t)i];
+        BranchLayout &bl = R.layouts[(size_t)c];
+        bl.n = (int)steps[(size_t)i].N.size();
+        bl.k = (int)steps[(size_t)i].K.size();
+        bl.bits = steps[(size_t)i].N;
+        bl.bits.insert(bl.bits.end(), steps[(size_t)i].K.begin(), steps[(size_t)i].K.end());
+        branch_of_step[(size_t)i] = c;
+    }
+    std::vector<int> L0;
+    {
+        std::vector<int> e0 = B[(size_t)s.seed_cluster].list();
+        L0 = sort_by_next_use(e0, steps, 0);
+        BranchLayout &bl = R.layouts[(size_t)s.seed_cluster];
+        bl.bits = L0;
+        bl.n = (int)L0.size();
+        bl.k = 0;
+    }
+    for (size_t c = 0; c < s.clusters.size(); ++c) {
+        BranchLayout &bl = R.layouts[c];
+        for (int e : (s.clusters[c].out & sl).list()) {
+            // slice-bit order = position in sliced_list
+            bl.sliced_edges.push_back(e);
+        }
+        std::sort(bl.sliced_edges.begin(), bl.sliced_edges.end(), [&](int a, int b) {
+            return std::find(s.sliced_list.begin(), s.sliced_list.end(), a) <
+                   std::find(s.sliced_list.begin(), s.sliced_list.end(), b);
+        });
+        for (int e : bl.sliced_edges) bl.bits.push_back(e);
+        for (int leaf : s.clusters[c].leaves)
+            if (net.leaves[(size_t)leaf].kind == LEAF_PROJ) bl.prefix_dependent = true;
+        if ((int)bl.sliced_edges.size() > MAX_BRANCH_SLICED)
+            fail(TN_ERR_UNSUPPORTED, "a branch carries too many sliced edges");
+    }
+
+    // ---------------- plain mode: per step a permute to [K | rest] then a GEMM
+    {
+        std::vector<int> lay = L0;
+        for (int i = 0; i < L; ++i) {
+            const StepSets &st = steps[(size_t)i];
+            std::vector<int> perm_out = st.K;  // kappa order
+            for (int e : lay)
+                if (std::find(st.K.begin(), st.K.end(), e) == st.K.end()) perm_out.push_back(e);
+            int r = (int)lay.size();
+            int c = std::min(C_BITS, r);
+            std::set<int> tile;
+            for (int p = 0; p < c; ++p) {
+                tile.insert(lay[(size_t)p]);
+                tile.insert(perm_out[(size_t)p]);
+            }
+            DevPass P = build_pass(lay, perm_out, c, c, tile, {}, steps, branch_of_step,
+                                   R.sp.chunk_table);
+            if (i == 0) P.in_branch = s.seed_cluster;
+            R.sp.plain_passes.push_back(P);
+            ExecStep es{};
+            es.permute_pass = (int)R.sp.plain_passes.size() - 1;
+            es.branch = branch_of_step[(size_t)i];
+            es.k = (int)st.K.size();
+            es.n = (int)st.N.size();
+            es.M = 1ll << (r - es.k);
+            es.r_in = st.r_in;
+            es.r_out = st.r_out;
+            R.sp.plain_steps.push_back(es);
+            R.sp.bytes_plain += 8.0 * (2.0 * std::exp2(r) + std::exp2(r) + std::exp2(st.r_out));
+            // GEMM output layout: [N (nu order) | rest (m order)]
+            std::vector<int> nl = st.N;
+            for (size_t p = st.K.size(); p < perm_out.size(); ++p) nl.push_back(perm_out[p]);
+            lay = nl;
+        }
+        if (L == 0) {
+            // no stem step: a single identity pass from the seed
+            int r = (int)lay.size();
+            int c = std::min(C_BITS, r);
+            std::set<int> tile(lay.begin(), lay.begin() + c);
+            DevPass P = build_pass(lay, lay, c, c, tile, {}, steps, branch_of_step, R.sp.chunk_table);
+            P.in_branch = s.seed_cluster;
+            R.sp.plain_passes.push_back(P);
+        }
+        R.sp.final_layout_plain = lay;
+    }
+
+    // ---------------- fused mode
+    {
+        std::vector<int> lay = L0;
+        int i = 0;
+        bool first = true;
+        R.sp.step_pass.assign((size_t)L, -1);
+        R.sp.step_gemm.assign((size_t)L, 0);
+        while (i < L || (L == 0 && first)) {
+            const int r = (int)lay.size();
+            const int c_in = std::min(C_BITS, r);
+            if (L > 0) {
+                const StepSets &st = steps[(size_t)i];
+                int k = (int)st.K.size(), n = (int)st.N.size();
+                if (k > MAX_STEP_K || n > MAX_STEP_K || k == 0 || k >= gemm_min || n >= gemm_min) {
+                    // GEMM step: permute to [K | rest], then GEMM -> [N | rest]
+                    std::vector<int> perm_out = st.K;
+                    for (int e : lay)
+                        if (std::find(st.K.begin(), st.K.end(), e) == st.K.end())
+                            perm_out.push_back(e);
+                    std::set<int> tile;
+                    for (int p = 0; p < c_in; ++p) {
+                        tile.insert(lay[(size_t)p]);
+                        tile.insert(perm_out[(size_t)p]);
+                    }
+                    DevPass P = build_pass(lay, perm_out, c_in, c_in, tile, {}, steps,
+                                           branch_of_step, R.sp.chunk_table);
+                    if (first) P.in_branch = s.seed_cluster;
+                    first = false;
+                    R.sp.fused_passes.push_back(P);
+                    FusedItem fp{0, (int)R.sp.fused_passes.size() - 1, -1, 0, 0, 0, r, r};
+                    R.sp.fused_items.push_back(fp);
+                    FusedItem g{1, -1, branch_of_step[(size_t)i], k, n, 1ll << (r - k), st.r_in,
+                                st.r_out};
+                    R.sp.fused_items.push_back(g);
+                    R.sp.bytes_fused += 8.0 * (2.0 * std::exp2(r) + std::exp2(r) + std::exp2(st.r_out));
+                    R.sp.step_gemm[(size_t)i] = 1;
+                    std::vector<int> nl = st.N;
+                    for (size_t p = st.K.size(); p < perm_out.size(); ++p) nl.push_back(perm_out[p]);
+                    lay = nl;
+                    ++i;
+                    continue;
+                }
+            }
+            // grow a group of fusable steps
+            std::set<int> in_tile(lay.begin(), lay.begin() + c_in);
+            std::vector<int> group;
+            {
+                // simulate tile states
+                std::set<int> in_set(lay.begin(), lay.end());
+                int j = i;
+                while (j < L && (int)group.size() < max_steps) {
+                    const StepSets &st = steps[(size_t)j];
+                    int k = (int)st.K.size(), n = (int)st.N.size();
+                    if (k > MAX_STEP_K || n > MAX_STEP_K || k == 0 || k >= gemm_min || n >= gemm_min)
+                        break;
+                    std::set<int> trial = in_tile;
+                    // edges needed from the input: K_j edges that are input edges
+                    for (int e : st.K)
+                        if (in_set.count(e)) trial.insert(e);
+                    // check tile sizes through the group + this step
+                    std::vector<int> g2 = group;
+                    g2.push_back(j);
+                    std::set<int> cur = trial;
+                    int mx = (int)cur.size();
+                    bool ok = true;
+                    for (int s2 : g2) {
+                        for (int e : steps[(size_t)s2].K)
+                            if (!cur.count(e)) ok = false;
+                        for (int e : steps[(size_t)s2].K) cur.erase(e);
+                        for (int e : steps[(size_t)s2].N) cur.insert(e);
+                        mx = std::max(mx, (int)cur.size());
+                    }
+                    if (!ok || mx > T_MAX) break;
+                    // rest bits of each step must be <= 12
+                    in_tile = trial;
+                    group.push_back(j);
+                    ++j;
+                }
+            }
+            if (group.empty() && L > 0) {
+                // the single step does not fit the tile: fall back to a GEMM step
+                const StepSets &st = steps[(size_t)i];
+                int k = (int)st.K.size(), n = (int)st.N.size();
+                std::vector<int> perm_out = st.K;
+                for (int e : lay)
+                    if (std::find(st.K.begin(), st.K.end(), e) == st.K.end()) perm_out.push_back(e);
+                std::set<int> tile;
+                for (int p = 0; p < c_in; ++p) {
+                    tile.insert(lay[(size_t)p]);
+                    tile.insert(perm_out[(size_t)p]);
+                }
+                DevPass P = build_pass(lay, perm_out, c_in, c_in, tile, {}, steps, branch_of_step,
+                                       R.sp.chunk_table);
+                if (first) P.in_branch = s.seed_cluster;
+                first = false;
+                R.sp.fused_passes.push_back(P);
+                R.sp.fused_items.push_back({0, (int)R.sp.fused_passes.size() - 1, -1, 0, 0, 0, r, r});
+                R.sp.fused_items.push_back(
+                    {1, -1, branch_of_step[(size_t)i], k, n, 1ll << (r - k), st.r_in, st.r_out});
+                R.sp.bytes_fused += 8.0 * (2.0 * std::exp2(r) + std::exp2(r) + std::exp2(st.r_out));
+                R.sp.step_gemm[(size_t)i] = 1;
+                std::vector<int> nl = st.N;
+                for (size_t p = st.K.size(); p < perm_out.size(); ++p) nl.push_back(perm_out[p]);
+                lay = nl;
+                ++i;
+                continue;
+            }
+            // output edges after the group
+            std::set<int> cur = in_tile;
+            std::set<int> out_all(lay.begin(), lay.end());
+            for (int s2 : group) {
+                for (int e : steps[(size_t)s2].K) {
+                    cur.erase(e);
+                    out_all.erase(e);
+                }
+                for (int e : steps[(size_t)s2].N) {
+                    cur.insert(e);
+                    out_all.insert(e);
+                }
+            }
+            int next = group.empty() ? i : group.back() + 1;
+            std::vector<int> tile_out(cur.begin(), cur.end());
+            tile_out = sort_by_next_use(tile_out, steps, next);
+            int c_out = std::min(C_BITS, (int)tile_out.size());
+            std::vector<int> low(tile_out.begin(), tile_out.begin() + c_out);
+            std::vector<int> others;
+            for (int e : out_all)
+                if (std::find(low.begin(), low.end(), e) == low.end()) others.push_back(e);
+            others = sort_by_next_use(others, steps, next);
+            std::vector<int> Lout = low;
+            Lout.insert(Lout.end(), others.begin(), others.end());
+            DevPass P = build_pass(lay, Lout, c_in, c_out, in_tile, group, steps, branch_of_step,
+                                   R.sp.chunk_table);
+            if (first) P.in_branch = s.seed_cluster;
+            first = false;
+            R.sp.fused_passes.push_back(P);
+            int pidx = (int)R.sp.fused_passes.size() - 1;
+            R.sp.fused_items.push_back({0, pidx, -1, 0, 0, 0, r, (int)Lout.size()});
+            R.sp.bytes_fused += 8.0 * (std::exp2(r) + std::exp2((double)Lout.size()));
+            for (int s2 : group) R.sp.step_pass[(size_t)s2] = pidx;
+            lay = Lout;
+            i = next;
+            if (L == 0) break;
+        }
+        R.sp.final_layout_fused = lay;
+    }
+    for (auto &P : R.sp.plain_passes) validate_pass(P, R.sp.chunk_table);
+    for (auto &P : R.sp.fused_passes) validate_pass(P, R.sp.chunk_table);
+    return R;
+}
+
+}  // namespace tn

@@ -1,0 +1,285 @@
+"""GPU parity: the CUDA stem path (through the C interface) against the FP64
+oracle, element by element, on seeded inputs.
+
+Tolerance: relative L2 error <= 1e-5 for the FP32 path (the stated bound for
+the FP32-accurate path). Data movement (permutation) must be bit-exact.
+"""
+
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2005_06787_gb300 as P
+from synthetic.circuits import (CONFIGS, Circuit, config_circuit, grid_layout, random_bits,
+                                random_circuit, random_complex)
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    P.build()
+    P.load()
+    torch.cuda.set_device(0)
+
+
+def rel_l2(a, b):
+    a = np.asarray(a).reshape(-1)
+    b = np.asarray(b).reshape(-1)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def run(plan, s0, s1, mode="fused", prec="fp32", device=True, accumulate=False, out=None):
+    info = P.tn_plan_info(plan)
+    n = max(info["n_prefixes"], 1) << info["n_open"]
+    if out is None:
+        out = torch.zeros(2 * n, dtype=torch.float64, device="cuda" if device else "cpu")
+    P.tn_contract_stem(plan, s0, s1, out, prec=prec, mode=mode, accumulate=accumulate)
+    torch.cuda.synchronize()
+    return out.cpu().numpy().view(np.complex128).reshape(max(info["n_prefixes"], 1), -1)
+
+
+# ------------------------------------------------------------------ kernels
+
+@pytest.mark.parametrize("rank,seed", [(1, 1), (5, 2), (11, 3), (17, 4), (20, 5)])
+def test_permute_bit_exact(rank, seed):
+    rng = np.random.default_rng(seed)
+    perm = rng.permutation(rank).astype(np.int32)
+    x = random_complex((1 << rank,), seed, np.complex64)
+    xin = torch.from_numpy(x.view(np.float32).copy()).cuda()
+    xout = torch.empty_like(xin)
+    P.tn_permute(xin, xout, rank, perm)
+    torch.cuda.synchronize()
+    got = xout.cpu().numpy().view(np.complex64)
+    # input bit j -> output bit perm[j]; numpy axes are MSB first
+    t = x.reshape((2,) * rank)
+    axes_in_bit = list(range(rank))  # bit j <-> axis rank-1-j
+    out_axes = [0] * rank
+    for j in axes_in_bit:
+        out_axes[rank - 1 - perm[j]] = rank - 1 - j
+    ref = np.transpose(t, out_axes).reshape(-1)
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("M,K,N,batch", [(1000, 4, 4, 1), (4096, 16, 16, 2), (777, 3, 5, 3),
+                                         (65, 64, 300, 1), (1, 1, 1, 1), (5000, 2, 1, 1)])
+def test_cgemm_simt_matches_fp64(M, K, N, batch):
+    A = random_complex((batch, M, K), 11, np.complex64)
+    B = random_complex((batch, K, N), 12, np.complex64)
+    dA = torch.from_numpy(A.view(np.float32).copy()).cuda()
+    dB = torch.from_numpy(B.view(np.float32).copy()).cuda()
+    dC = torch.zeros(batch * M * N * 2, dtype=torch.float32, device="cuda")
+    P.tn_cgemm(dA, dB, dC, M, K, N, batch, M * K, K * N, M * N)
+    torch.cuda.synchronize()
+    got = dC.cpu().numpy().view(np.complex64).reshape(batch, M, N)
+    ref = np.matmul(A.astype(np.complex128), B.astype(np.complex128))
+    assert rel_l2(got, ref) < TOL
+
+
+def test_linear_xeb_kernel():
+    a = random_complex((4096,), 3) / 64.0
+    d = torch.from_numpy(a.view(np.float64).copy()).cuda()
+    got = P.tn_linear_xeb(d, 12)
+    ref = oracle.linear_xeb(np.abs(a) ** 2, 12)
+    assert got == pytest.approx(ref, rel=1e-12)
+
+
+# ------------------------------------------------------------ stem, small
+
+def _plan(c, oq, closed, **kw):
+    net = P.tn_build_network(c, oq, closed)
+    plan = P.tn_plan_create(net, **kw)
+    return net, plan
+
+
+@pytest.mark.parametrize("mode", ["fused", "plain"])
+def test_grid4x4_m8_closed_amplitudes(mode):
+    # 16 qubits, 8 cycles, 64 seeded bitstrings as 64 closed prefixes
+    name = "grid4x4_m8"
+    cfg = CONFIGS[name]
+    c = config_circuit(name)
+    bits = [list(random_bits(16, cfg["bit_seed"] + i)) for i in range(cfg["bitstrings"])]
+    net, plan = _plan(c, [], bits[0], cw_limit=30, restarts=4)
+    P.tn_plan_prepare(plan, np.asarray(bits, dtype=np.uint8))
+    got = run(plan, 0, 1, mode=mode)[:, 0]
+    psi = oracle.statevector(c)
+    ref = np.array([oracle.sv_amplitudes(c, [], b, psi)[0] for b in bits])
+    assert rel_l2(got, ref) < TOL
+
+
+@pytest.mark.parametrize("mode", ["fused", "plain"])
+@pytest.mark.parametrize("rows,cols,m,cw,n_open,seed", [(3, 4, 8, 7, 3, 1), (4, 4, 10, 9, 6, 2),
+                                                        (3, 3, 6, 5, 0, 3), (2, 3, 4, 6, 6, 4)])
+def test_sliced_partials_and_sum(mode, rows, cols, m, cw, n_open, seed):
+    c = random_circuit(grid_layout(rows, cols), m, 50 + seed)
+    oq = list(range(n_open))
+    cb = list(random_bits(c.n_qubits - n_open, seed))
+    net, plan = _plan(c, oq, cb, cw_limit=cw, restarts=3, min_sliced=2 if n_open < c.n_qubits else 0)
+    P.tn_plan_prepare(plan)
+    info = P.tn_plan_info(plan)
+    nsl = info["n_sliced"]
+    _, sl = P.tn_plan_export(plan)
+    _, _, q, s = net.info()
+    sliced = [(int(q[e]), int(s[e])) for e in sl]
+    psi = oracle.statevector(c)
+    ref = oracle.sv_amplitudes(c, oq, cb, psi)
+    tot = run(plan, 0, 1 << nsl, mode=mode)[0]
+    assert rel_l2(tot, ref) < TOL
+    for sid in sorted({0, (1 << nsl) - 1, (1 << nsl) // 3}):
+        part = run(plan, sid, sid + 1, mode=mode)[0]
+        pref = oracle.sv_amplitudes(c, oq, cb, projectors=oracle.slice_assignment(sliced, sid))
+        if np.linalg.norm(pref) > 1e-12:
+            assert rel_l2(part, pref) < TOL
+        else:
+            assert np.linalg.norm(part) < 1e-6
+
+
+def test_ranges_add_and_host_output():
+    c = random_circuit(grid_layout(3, 4), 8, 71)
+    oq = [0, 1, 2, 3]
+    cb = list(random_bits(8, 9))
+    net, plan = _plan(c, oq, cb, cw_limit=7, restarts=3, min_sliced=3)
+    P.tn_plan_prepare(plan)
+    nsl = P.tn_plan_info(plan)["n_sliced"]
+    full = run(plan, 0, 1 << nsl)
+    out = torch.zeros(2 * 16, dtype=torch.float64, device="cuda")
+    P.tn_contract_stem(plan, 0, 3, out)
+    P.tn_contract_stem(plan, 3, 1 << nsl, out, accumulate=True)
+    torch.cuda.synchronize()
+    acc = out.cpu().numpy().view(np.complex128)
+    assert rel_l2(acc, full[0]) < 1e-12
+    host = np.zeros(32)
+    P.tn_contract_stem(plan, 0, 1 << nsl, host)
+    assert rel_l2(host.view(np.complex128), full[0]) < 1e-12
+    empty = run(plan, 2, 2)
+    assert np.all(empty == 0)
+    with pytest.raises(P.TnError):
+        P.tn_contract_stem(plan, 0, (1 << nsl) + 1, out)
+    with pytest.raises(P.TnError):
+        P.tn_contract_stem(plan, 3, 2, out)
+
+
+def test_all_qubits_open_is_statevector():
+    c = random_circuit(grid_layout(2, 3), 6, 5)
+    oq = list(range(6))
+    net, plan = _plan(c, oq, [], cw_limit=8, restarts=2)
+    P.tn_plan_prepare(plan)
+    got = run(plan, 0, 1 << P.tn_plan_info(plan)["n_sliced"])[0]
+    assert rel_l2(got, oracle.statevector(c)) < TOL
+
+
+def test_prefix_batch_equals_single_prefixes():
+    c = random_circuit(grid_layout(3, 4), 8, 77)
+    oq = [0, 5]
+    pres = [list(random_bits(10, 300 + i)) for i in range(5)]
+    net, plan = _plan(c, oq, pres[0], cw_limit=6, restarts=2, slice_batch=3)
+    P.tn_plan_prepare(plan, np.asarray(pres, dtype=np.uint8))
+    nsl = P.tn_plan_info(plan)["n_sliced"]
+    got = run(plan, 0, 1 << nsl)
+    psi = oracle.statevector(c)
+    for i, p in enumerate(pres):
+        assert rel_l2(got[i], oracle.sv_amplitudes(c, oq, p, psi)) < TOL
+
+
+# ------------------------------------------------------------ 30-qubit grid
+
+def test_grid5x6_m14_against_stored_statevector():
+    path = os.path.join(GOLD, "grid5x6_m14_amps.json")
+    g = json.load(open(path))
+    name = g["workload"]
+    c = config_circuit(name)
+    oq = g["open_qubits"]
+    pres = np.asarray(g["prefixes"], dtype=np.uint8)
+    net, plan = _plan(c, oq, list(pres[0]), cw_limit=30, min_sliced=CONFIGS[name]["n_sliced"],
+                      restarts=4)
+    P.tn_plan_prepare(plan, pres)
+    info = P.tn_plan_info(plan)
+    assert info["n_sliced"] == CONFIGS[name]["n_sliced"]
+    got = run(plan, 0, 1 << info["n_sliced"])
+    ref = np.asarray(g["amps_re"]) + 1j * np.asarray(g["amps_im"])
+    assert rel_l2(got, ref) < TOL
+
+
+# ----------------------------------------------- full size, closed form
+# With fSim(0, 0) = identity the network keeps its structure (the planner
+# sees only structure, so the plan and every launch are the full-size ones)
+# but its value factorises over qubits: a partial amplitude is the product
+# over qubits of <x_q| ... P_v ... |0>, the projectors P_v sitting on the
+# sliced wire segments of that qubit.
+
+def _closed_form(c, oq, closed_bits, sliced_by_wire, slice_id):
+    n = c.n_qubits
+    # per-qubit list of gate matrices in time order (identity for 2q gates)
+    events = [[] for _ in range(n)]
+    for t in range(c.n_cycles + 1):
+        for q in range(n):
+            events[q].append(oracle.gate_1q(c.gates_1q[t][q]))
+        if t == c.n_cycles:
+            break
+        for (a, b) in c.pairs[t]:
+            events[a].append(np.eye(2))
+            events[b].append(np.eye(2))
+    closed = [q for q in range(n) if q not in set(oq)]
+    vec = {}
+    for q in range(n):
+        v = np.array([1.0, 0.0], dtype=complex)
+        for s_idx, G in enumerate(events[q]):
+            key = (q, s_idx)
+            if key in sliced_by_wire:
+                bit = (slice_id >> sliced_by_wire[key]) & 1
+                v = v * (np.arange(2) == bit)
+            v = G @ v
+        key = (q, len(events[q]))
+        if key in sliced_by_wire:
+            bit = (slice_id >> sliced_by_wire[key]) & 1
+            v = v * (np.arange(2) == bit)
+        vec[q] = v
+    scal = 1.0 + 0j
+    for q, b in zip(closed, closed_bits):
+        scal *= vec[q][int(b)]
+    out = np.ones(1, dtype=complex)
+    for q in oq:
+        out = np.kron(out, vec[q])
+    return scal * out
+
+
+@pytest.mark.parametrize("name", ["diag53_m14", "diag53_m12"])
+def test_full_size_plan_identity_fsim_closed_form(name):
+    from bench import plan_options
+    cfg = CONFIGS[name]
+    c = config_circuit(name)
+    c0 = Circuit(c.n_qubits, c.n_cycles, c.gates_1q, c.pairs, 0.0, 0.0, c.layout)
+    oq = c.layout.open_qubits(cfg["n_open"])
+    cb = list(random_bits(c.n_qubits - len(oq), cfg["bit_seed"]))
+    opts = plan_options(name)
+    net_ref, plan_ref = _plan(c, oq, cb, **opts)
+    net, plan = _plan(c0, oq, cb, **opts)
+    o1, s1 = P.tn_plan_export(plan_ref)
+    o2, s2 = P.tn_plan_export(plan)
+    assert np.array_equal(o1, o2) and np.array_equal(s1, s2)
+    P.tn_plan_prepare(plan)
+    info = P.tn_plan_info(plan)
+    _, _, q, s = net.info()
+    wires = {(int(q[e]), int(s[e])): j for j, e in enumerate(s2)}
+    nsl = info["n_sliced"]
+    ids = [0, 1, (1 << nsl) - 1, 12345 % (1 << nsl)]
+    for sid in ids:
+        got = run(plan, sid, sid + 1)[0]
+        ref = _closed_form(c0, oq, cb, wires, sid)
+        if np.linalg.norm(ref) > 1e-30:
+            assert rel_l2(got, ref) < TOL, (sid, rel_l2(got, ref))
+        else:
+            assert np.linalg.norm(got) <= 1e-6 * (2.0 ** (-c.n_qubits / 2))
+    # a whole batch at the bench's batch size
+    sb = info["batch_items"]
+    got = run(plan, 0, sb)[0]
+    ref = sum(_closed_form(c0, oq, cb, wires, sid) for sid in range(sb))
+    assert rel_l2(got, ref) < TOL

@@ -1,0 +1,148 @@
+"""Host-side tests of libtnstem (no GPU): the C interface loads and exports
+every declared symbol, the planner's schemes are valid contraction trees whose
+value (computed by the oracle) equals the state-vector amplitudes, reported
+costs equal the oracle's tc/cw, and bad input is rejected with a status."""
+
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2005_06787_gb300 as P
+from synthetic.circuits import (CONFIGS, config_circuit, grid_layout, random_bits,
+                                random_circuit)
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    P.build()
+    P.load()
+
+
+def test_library_exports_every_header_symbol():
+    hdr = open(os.path.join(ROOT, "include", "tnstem.h")).read()
+    declared = set(re.findall(r"\b(tn_[a-z0-9_]+)\s*\(", hdr))
+    assert declared, "no declarations parsed"
+    lib = P.load()
+    for name in sorted(declared):
+        assert hasattr(lib, name), f"libtnstem.so lacks {name}"
+    assert set(P.EXPORTED) <= declared
+
+
+def _net(c, oq, seed):
+    cb = list(random_bits(c.n_qubits - len(oq), seed))
+    return P.tn_build_network(c, oq, cb), cb
+
+
+def _oracle_edges(net):
+    _, _, q, s = net.info()
+    return [(int(a), int(b)) for a, b in zip(q, s)]
+
+
+@pytest.mark.parametrize("rows,cols,m,cw,n_open", [(3, 4, 8, 7, 3), (3, 3, 6, 5, 2),
+                                                    (2, 4, 5, 4, 0), (4, 4, 8, 9, 4)])
+def test_planned_scheme_value_equals_statevector(rows, cols, m, cw, n_open):
+    c = random_circuit(grid_layout(rows, cols), m, rows * 100 + m)
+    oq = list(range(n_open))
+    net, cb = _net(c, oq, 17)
+    plan = P.tn_plan_create(net, cw_limit=cw, restarts=4)
+    info = P.tn_plan_info(plan)
+    assert info["cw"] <= cw
+    order, sl = P.tn_plan_export(plan)
+    edges = _oracle_edges(net)
+    sliced = [edges[e] for e in sl]
+    onet = oracle.build_network(c, oq, cb)
+    tot = oracle.contract_sliced_sum(onet, sliced, [tuple(x) for x in order])
+    ref = oracle.sv_amplitudes(c, oq, cb)
+    np.testing.assert_allclose(tot.reshape(-1), ref, atol=1e-13)
+    tc, ocw = oracle.tree_cost(onet.edges, onet.open_edges, [tuple(x) for x in order], sliced)
+    assert ocw == info["cw"]
+    assert math.log2(tc) == pytest.approx(info["log2_tc"], abs=1e-9)
+
+
+def test_given_order_round_trip():
+    c = random_circuit(grid_layout(3, 4), 8, 3)
+    net, _ = _net(c, [0, 1], 5)
+    p1 = P.tn_plan_create(net, cw_limit=7, restarts=3)
+    order, sl = P.tn_plan_export(p1)
+    p2 = P.tn_plan_create(net, order=[tuple(x) for x in order], sliced_edges=list(sl))
+    i1, i2 = P.tn_plan_info(p1), P.tn_plan_info(p2)
+    assert i1["log2_tc"] == pytest.approx(i2["log2_tc"])
+    assert i1["cw"] == i2["cw"]
+    o2, s2 = P.tn_plan_export(p2)
+    onet = oracle.build_network(c, [0, 1], list(random_bits(10, 5)))
+    edges = _oracle_edges(net)
+    v = oracle.contract_sliced_sum(onet, [edges[e] for e in s2], [tuple(x) for x in o2])
+    np.testing.assert_allclose(v.reshape(-1), oracle.sv_amplitudes(c, [0, 1], list(random_bits(10, 5))),
+                               atol=1e-13)
+
+
+def test_plan_shapes_of_paper_workloads():
+    # 53-qubit, 12-cycle stand-in: the stem fits the width limit by slicing
+    name = "diag53_m12"
+    cfg = CONFIGS[name]
+    c = config_circuit(name)
+    oq = c.layout.open_qubits(cfg["n_open"])
+    net, _ = _net(c, oq, cfg["bit_seed"])
+    plan = P.tn_plan_create(net, cw_limit=cfg["cw_limit"], restarts=2)
+    info = P.tn_plan_info(plan)
+    assert info["cw"] <= cfg["cw_limit"]
+    assert info["n_sliced"] >= 1
+    steps = P.tn_plan_steps(plan)
+    assert len(steps) == info["n_stem_steps"]
+    # every step is a (k, n) absorption that keeps ranks consistent
+    for a, b in zip(steps, steps[1:]):
+        assert a["r_out"] == b["r_in"]
+    for s in steps:
+        assert s["r_out"] == s["r_in"] - s["k"] + s["n"]
+    assert steps[-1]["r_out"] == cfg["n_open"]
+    # fused passes read and write each stem tensor once per group of steps
+    assert info["stem_bytes_fused"] < info["stem_bytes_plain"] / 4
+
+
+def test_network_info_wire_segments():
+    c = random_circuit(grid_layout(2, 2), 2, 9)
+    net, _ = _net(c, [1], 3)
+    nl, ne, q, s = net.info()
+    onet = oracle.build_network(c, [1], list(random_bits(3, 3)))
+    assert nl == len(onet.tensors)
+    assert sorted(zip(q.tolist(), s.tolist())) == sorted(onet.all_edges())
+
+
+def test_bad_inputs_are_rejected():
+    c = random_circuit(grid_layout(2, 2), 2, 9)
+    with pytest.raises(P.TnError) as e:
+        P.tn_build_network(c, [7], [0, 0, 0])
+    assert e.value.status == 1
+    with pytest.raises(P.TnError):
+        P.tn_build_network(c, [0, 0], [0, 0])
+    with pytest.raises(P.TnError):
+        P.tn_build_network(c, [0], [0, 2, 0])
+    net, _ = _net(c, [0], 1)
+    nl = net.info()[0]
+    with pytest.raises(P.TnError):
+        P.tn_plan_create(net, order=[(0, 0)] * (nl - 1))
+    with pytest.raises(P.TnError):
+        P.tn_plan_create(net, order=[(0, 1)])
+    _, _, q, s = net.info()
+    open_edge = [e for e in range(len(q)) if (q[e], s[e]) == (0, max(s[q == 0]))][0]
+    good = P.tn_plan_create(net, cw_limit=8)
+    order, _ = P.tn_plan_export(good)
+    with pytest.raises(P.TnError):
+        P.tn_plan_create(net, order=[tuple(x) for x in order], sliced_edges=[open_edge])
+    out = np.zeros(4)
+    with pytest.raises(P.TnError):  # not prepared
+        P.tn_contract_stem(good, 0, 1, out)
+
+
+def test_infeasible_width_reports_status():
+    c = random_circuit(grid_layout(3, 3), 6, 4)
+    net, _ = _net(c, list(range(9)), 0)  # all open: width >= 9 with no slicing allowed
+    with pytest.raises(P.TnError) as e:
+        P.tn_plan_create(net, cw_limit=6, max_sliced=1)
+    assert e.value.status == 4
