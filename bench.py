@@ -235,6 +235,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--ref-budget", type=float, default=60.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--tile-bits", type=int, default=0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -261,7 +262,10 @@ def main():
     c, oq, cb = workload_inputs(name)
     net = P.tn_build_network(c, oq, cb)
     t0 = time.perf_counter()
-    plan = P.tn_plan_create(net, **plan_options(name))
+    popts = plan_options(name)
+    if args.tile_bits:
+        popts["tile_bits"] = args.tile_bits
+    plan = P.tn_plan_create(net, **popts)
     plan_s = time.perf_counter() - t0
     P.tn_plan_prepare(plan, stream=stream)
     torch.cuda.synchronize()
@@ -340,6 +344,16 @@ def main():
         d["bytes"] += r["bytes"]
         d["flops"] += r["flops"]
         d["launches"] += 1
+    plain_recs = P.tn_plan_profile(plan, base, prec="fp32", mode="plain", stream=stream)
+    plain_kind = {}
+    for r in plain_recs:
+        k = {0: "pass", 1: "gemm", 2: "permute", 3: "slice_sum"}[r["kind"]]
+        d = plain_kind.setdefault(k, {"ms": 0.0, "bytes": 0.0, "launches": 0})
+        d["ms"] += r["ms"]
+        d["bytes"] += r["bytes"]
+        d["launches"] += 1
+    for d in plain_kind.values():
+        d["gbs"] = d["bytes"] / (d["ms"] / 1e3) / 1e9 if d["ms"] else None
     dom = max(by_kind, key=lambda k: by_kind[k]["ms"])
     peaks, peak_kind = measured_peaks()
     d = by_kind[dom]
@@ -384,6 +398,7 @@ def main():
                     "d2h_bytes_per_step": 16 * nb},
             "roofline": roofline,
             "launch_breakdown": by_kind,
+            "plain_breakdown": plain_kind,
             "cpu_baseline": cpu,
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks,

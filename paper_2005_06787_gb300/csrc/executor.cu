@@ -103,7 +103,10 @@ void plan_prepare(Plan &p, const uint8_t *prefixes, int n_prefixes, cudaStream_t
         leaf_total += (int64_t)net.leaves[(size_t)i].vals.size();
         leaf_total = (leaf_total + 1) & ~1ll;
     }
-    std::vector<float2> h_leaf((size_t)(leaf_total * n_prefixes));
+    // leaves and branch intermediates stay in FP64; each branch is rounded to
+    // FP32 once, when it is stored (rounding every gate separately would bias
+    // the result: 1/sqrt(2) rounds the same way in every single-qubit gate)
+    std::vector<double2> h_leaf((size_t)(leaf_total * n_prefixes));
     for (int pp = 0; pp < n_prefixes; ++pp)
         for (int i = 0; i < L; ++i) {
             const Leaf &lf = net.leaves[(size_t)i];
@@ -114,12 +117,12 @@ void plan_prepare(Plan &p, const uint8_t *prefixes, int n_prefixes, cudaStream_t
                     x = (v == (size_t)b) ? 1.0 : 0.0;
                 }
                 h_leaf[(size_t)(pp * leaf_total + leaf_off[(size_t)i] + (int64_t)v)] =
-                    make_float2((float)x.real(), (float)x.imag());
+                    make_double2(x.real(), x.imag());
             }
         }
-    float2 *d_leaf = nullptr;
-    TN_CUDA(cudaMalloc(&d_leaf, h_leaf.size() * sizeof(float2)));
-    TN_CUDA(cudaMemcpyAsync(d_leaf, h_leaf.data(), h_leaf.size() * sizeof(float2),
+    double2 *d_leaf = nullptr;
+    TN_CUDA(cudaMalloc(&d_leaf, h_leaf.size() * sizeof(double2)));
+    TN_CUDA(cudaMemcpyAsync(d_leaf, h_leaf.data(), h_leaf.size() * sizeof(double2),
                             cudaMemcpyHostToDevice, st));
 
     // ---- branch pool layout
@@ -191,8 +194,8 @@ void plan_prepare(Plan &p, const uint8_t *prefixes, int n_prefixes, cudaStream_t
         node_layouts[(size_t)c] = lays;
         scratch_need = std::max(scratch_need, need);
     }
-    float2 *d_scratch = nullptr;
-    TN_CUDA(cudaMalloc(&d_scratch, (size_t)std::max<int64_t>(scratch_need, 64) * sizeof(float2)));
+    double2 *d_scratch = nullptr;
+    TN_CUDA(cudaMalloc(&d_scratch, (size_t)std::max<int64_t>(scratch_need, 64) * sizeof(double2)));
     for (int c = 0; c < C; ++c) {
         const Cluster &cl = p.scheme.clusters[(size_t)c];
         const BranchLayout &bl = p.layouts[(size_t)c];
@@ -201,32 +204,33 @@ void plan_prepare(Plan &p, const uint8_t *prefixes, int n_prefixes, cudaStream_t
         for (int pp = 0; pp < copies; ++pp) {
             float2 *dst = p.d_pool + p.h_branches[(size_t)c].base +
                           (int64_t)pp * p.h_branches[(size_t)c].prefix_stride;
-            const float2 *leafbase = d_leaf + (int64_t)pp * leaf_total;
+            const double2 *leafbase = d_leaf + (int64_t)pp * leaf_total;
             if (cl.pairs.empty()) {
                 int leaf = cl.leaves[0];
                 SmallContract d = make_contract(leaf_layout(leaf), {}, bl.bits);
-                TN_CUDA(launch_small_contract(leafbase + leaf_off[(size_t)leaf], nullptr, dst, d, st));
+                TN_CUDA(launch_small_contract(leafbase + leaf_off[(size_t)leaf], nullptr, nullptr, dst,
+                                              d, st));
                 continue;
             }
-            std::vector<const float2 *> node_ptr;
+            std::vector<const double2 *> node_ptr;
             int64_t off = 0;
             for (size_t k = 0; k < cl.pairs.size(); ++k) {
-                auto ptr_of = [&](int ref) -> const float2 * {
+                auto ptr_of = [&](int ref) -> const double2 * {
                     return ref >= 0 ? leafbase + leaf_off[(size_t)ref] : node_ptr[(size_t)(-ref - 1)];
                 };
                 auto lay_of = [&](int ref) -> std::vector<int> {
                     return ref >= 0 ? leaf_layout(ref) : lays[(size_t)(-ref - 1)];
                 };
                 const auto &pr = cl.pairs[k];
-                float2 *out;
-                if (k + 1 == cl.pairs.size()) {
-                    out = dst;
-                } else {
+                const bool last = k + 1 == cl.pairs.size();
+                double2 *out = nullptr;
+                if (!last) {
                     out = d_scratch + off;
                     off += (((int64_t)1 << lays[k].size()) + 63) & ~63ll;
                 }
                 SmallContract d = make_contract(lay_of(pr.first), lay_of(pr.second), lays[k]);
-                TN_CUDA(launch_small_contract(ptr_of(pr.first), ptr_of(pr.second), out, d, st));
+                TN_CUDA(launch_small_contract(ptr_of(pr.first), ptr_of(pr.second), out,
+                                              last ? dst : nullptr, d, st));
                 node_ptr.push_back(out);
             }
         }

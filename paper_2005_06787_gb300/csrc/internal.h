@@ -175,7 +175,17 @@ constexpr int MAX_TILE_BITS = 12;
 constexpr int MAX_BRANCH_SLICED = 24;
 constexpr int MAX_FREE = 40;
 
-// All offsets are in complex elements.
+// Shared-memory tiles are addressed through a bank swizzle: tile position p
+// lives at tile_swizzle(p) = p ^ (bits 4-7 of p) ^ rot2(bits 8-11 of p) in
+// the low four bits. The map is linear over GF(2), so offsets of disjoint bit
+// sets combine with XOR; it spreads power-of-two strides of 16 and 256
+// entries over all 16 eight-byte bank pairs.
+inline int tile_swizzle(int p) {
+    const int a = (p >> 4) & 15, b = (p >> 8) & 15;
+    return p ^ a ^ (((b << 2) | (b >> 2)) & 15);
+}
+
+// All offsets are in complex elements; tile offsets are swizzled positions.
 struct DevStep {
     int k, n, rest;
     int branch;                 // index into DevBranch table

@@ -29,6 +29,12 @@ __device__ __forceinline__ int64_t branch_offset(const DevBranch &b, int p, int6
 }
 
 // ---------------------------------------------------------------- fused pass
+// Tile bank swizzle (same map as tile_swizzle on the host).
+__device__ __forceinline__ int dev_swizzle(int p) {
+    const int a = (p >> 4) & 15, b = (p >> 8) & 15;
+    return p ^ a ^ (((b << 2) | (b >> 2)) & 15);
+}
+
 // One stem step inside the tile: for each rest index rho (thread-strided),
 // y[nu] = sum_kappa x[kappa] * B[kappa][nu], read at in-tile offsets
 // io(rho) + koff[kappa], written at oo(rho) + noff[nu].
@@ -41,16 +47,16 @@ __device__ __forceinline__ void step_body(const float2 *__restrict__ tin, float2
     for (int kk = 0; kk < NK; ++kk) koff[kk] = S.koff[kk];
     const int nrest = 1 << S.rest;
     for (int r = threadIdx.x; r < nrest; r += nt) {
-        const int io = S.in_lo[r & 63] + S.in_hi[r >> 6];
-        const int oo = S.out_lo[r & 63] + S.out_hi[r >> 6];
+        const int io = S.in_lo[r & 63] ^ S.in_hi[r >> 6];
+        const int oo = S.out_lo[r & 63] ^ S.out_hi[r >> 6];
         float2 x[NK];
 #pragma unroll
-        for (int kk = 0; kk < NK; ++kk) x[kk] = tin[io + koff[kk]];
+        for (int kk = 0; kk < NK; ++kk) x[kk] = tin[io ^ koff[kk]];
         if constexpr (NN == 1) {
             float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
             for (int kk = 0; kk < NK; ++kk) cfma(acc, x[kk], Bm[kk]);
-            tout[oo + S.noff[0]] = acc;
+            tout[oo ^ S.noff[0]] = acc;
         } else {
             // two outputs per iteration; B[kappa][nu], B[kappa][nu+1] in one 16-byte load
 #pragma unroll 1
@@ -62,8 +68,8 @@ __device__ __forceinline__ void step_body(const float2 *__restrict__ tin, float2
                     cfma(a0, x[kk], make_float2(b.x, b.y));
                     cfma(a1, x[kk], make_float2(b.z, b.w));
                 }
-                tout[oo + S.noff[nn]] = a0;
-                tout[oo + S.noff[nn + 1]] = a1;
+                tout[oo ^ S.noff[nn]] = a0;
+                tout[oo ^ S.noff[nn + 1]] = a1;
             }
         }
     }
@@ -73,8 +79,8 @@ __device__ __forceinline__ void copy_body(const float2 *__restrict__ tin, float2
                                           const DevStep &S, int nt) {
     const int nrest = 1 << S.rest;
     for (int r = threadIdx.x; r < nrest; r += nt) {
-        const int io = S.in_lo[r & 63] + S.in_hi[r >> 6];
-        const int oo = S.out_lo[r & 63] + S.out_hi[r >> 6];
+        const int io = S.in_lo[r & 63] ^ S.in_hi[r >> 6];
+        const int oo = S.out_lo[r & 63] ^ S.out_hi[r >> 6];
         tout[oo] = tin[io];
     }
 }
@@ -167,11 +173,12 @@ pass_kernel(const DevPass *__restrict__ gpass, const int *__restrict__ chunks,
             for (int idx = threadIdx.x * 2; idx < tin_n; idx += PASS_THREADS * 2) {
                 const int j = idx >> P.c_in, w = idx & cin_mask;
                 const float4 v = *reinterpret_cast<const float4 *>(src + ib + cin_tab[j] + w);
-                *reinterpret_cast<float4 *>(tA + idx) = v;
+                tA[dev_swizzle(idx)] = make_float2(v.x, v.y);
+                tA[dev_swizzle(idx + 1)] = make_float2(v.z, v.w);
             }
         } else {
             for (int idx = threadIdx.x; idx < tin_n; idx += PASS_THREADS)
-                tA[idx] = src[ib + cin_tab[idx]];
+                tA[dev_swizzle(idx)] = src[ib + cin_tab[idx]];
         }
         __syncthreads();
         float2 *cur = tA, *nxt = tB;
@@ -185,12 +192,12 @@ pass_kernel(const DevPass *__restrict__ gpass, const int *__restrict__ chunks,
         if (P.c_out >= 1) {
             for (int idx = threadIdx.x * 2; idx < tout_n; idx += PASS_THREADS * 2) {
                 const int j = idx >> P.c_out, w = idx & cout_mask;
-                *reinterpret_cast<float4 *>(dst + ob + cout_tab[j] + w) =
-                    *reinterpret_cast<const float4 *>(cur + idx);
+                const float2 a = cur[dev_swizzle(idx)], b = cur[dev_swizzle(idx + 1)];
+                *reinterpret_cast<float4 *>(dst + ob + cout_tab[j] + w) = make_float4(a.x, a.y, b.x, b.y);
             }
         } else {
             for (int idx = threadIdx.x; idx < tout_n; idx += PASS_THREADS)
-                dst[ob + cout_tab[idx]] = cur[idx];
+                dst[ob + cout_tab[idx]] = cur[dev_swizzle(idx)];
         }
         __syncthreads();
     }
@@ -228,11 +235,13 @@ cudaError_t launch_pass(const DevPass *d_pass, const DevPass &h_pass, const int 
 }
 
 // ------------------------------------------------------- small contraction
-// Branch pre-computation (Supp. A.3): one pairwise step on small tensors,
-// C[o] = sum_c A[ia(o) + ja(c)] * B[ib(o) + jb(c)]; B == nullptr means a
-// permutation of A.
-__global__ void small_contract_kernel(const float2 *__restrict__ A, const float2 *__restrict__ B,
-                                      float2 *__restrict__ C, SmallContract d) {
+// Branch pre-computation (Supp. A.3): one pairwise step on small tensors in
+// FP64, C[o] = sum_c A[ia(o) + ja(c)] * B[ib(o) + jb(c)]; B == nullptr means
+// a permutation of A. The result is stored in FP64 (Cd) or rounded to FP32
+// (Cf) when it is a finished branch.
+__global__ void small_contract_kernel(const double2 *__restrict__ A, const double2 *__restrict__ B,
+                                      double2 *__restrict__ Cd, float2 *__restrict__ Cf,
+                                      SmallContract d) {
     const int64_t nout = (int64_t)1 << d.rc;
     const int64_t nsum = (int64_t)1 << d.k;
     for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < nout;
@@ -245,30 +254,40 @@ __global__ void small_contract_kernel(const float2 *__restrict__ A, const float2
             else
                 ib += (int64_t)1 << d.b_out[j];
         }
+        double re, im;
         if (!B) {
-            C[o] = A[ia];
-            continue;
+            re = A[ia].x;
+            im = A[ia].y;
+        } else {
+            re = 0.0;
+            im = 0.0;
+            for (int64_t c = 0; c < nsum; ++c) {
+                int64_t ja = ia, jb = ib;
+                for (int t = 0; t < d.k; ++t)
+                    if ((c >> t) & 1) {
+                        ja += (int64_t)1 << d.a_k[t];
+                        jb += (int64_t)1 << d.b_k[t];
+                    }
+                const double2 a = A[ja], b = B[jb];
+                re = fma(a.x, b.x, re);
+                re = fma(-a.y, b.y, re);
+                im = fma(a.x, b.y, im);
+                im = fma(a.y, b.x, im);
+            }
         }
-        float2 acc = make_float2(0.f, 0.f);
-        for (int64_t c = 0; c < nsum; ++c) {
-            int64_t ja = ia, jb = ib;
-            for (int t = 0; t < d.k; ++t)
-                if ((c >> t) & 1) {
-                    ja += (int64_t)1 << d.a_k[t];
-                    jb += (int64_t)1 << d.b_k[t];
-                }
-            cfma(acc, A[ja], B[jb]);
-        }
-        C[o] = acc;
+        if (Cf)
+            Cf[o] = make_float2((float)re, (float)im);
+        else
+            Cd[o] = make_double2(re, im);
     }
 }
 
-cudaError_t launch_small_contract(const float2 *A, const float2 *B, float2 *C,
+cudaError_t launch_small_contract(const double2 *A, const double2 *B, double2 *Cd, float2 *Cf,
                                   const SmallContract &d, cudaStream_t st) {
     const int64_t nout = (int64_t)1 << d.rc;
     const int threads = 256;
     const int64_t blocks = std::min<int64_t>((nout + threads - 1) / threads, 4096);
-    small_contract_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), threads, 0, st>>>(A, B, C, d);
+    small_contract_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), threads, 0, st>>>(A, B, Cd, Cf, d);
     return cudaGetLastError();
 }
 

@@ -36,7 +36,9 @@ cudaError_t launch_pass(const DevPass *d_pass, const DevPass &h_pass, const int 
                         const float2 *pool, const float2 *in, float2 *out, BatchArgs ba,
                         cudaStream_t st);
 
-cudaError_t launch_small_contract(const float2 *A, const float2 *B, float2 *C,
+// FP64 pairwise contraction for branch pre-computation; writes FP64 to Cd, or
+// rounds to FP32 into Cf when Cf is given.
+cudaError_t launch_small_contract(const double2 *A, const double2 *B, double2 *Cd, float2 *Cf,
                                   const SmallContract &d, cudaStream_t st);
 
 // Stem GEMM step over batch items: C_item[m][nu] = sum_kappa A_item[m][kappa] *

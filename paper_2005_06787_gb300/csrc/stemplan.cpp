@@ -30,17 +30,22 @@ int pos_of(const std::vector<int> &layout, int e) {
     return -1;
 }
 
-// Order edges by the index of the step that next contracts them (soonest
-// first; never = last), ties by edge id.
+// Index of the first step >= from that contracts e (never: 1 << 30).
+int next_use(int e, const std::vector<StepSets> &steps, int from) {
+    for (int i = from; i < (int)steps.size(); ++i)
+        for (int x : steps[(size_t)i].K)
+            if (x == e) return i;
+    return 1 << 30;
+}
+
+// Order edges by the step that next contracts them, soonest first (or latest
+// first), ties by edge id.
 std::vector<int> sort_by_next_use(std::vector<int> edges, const std::vector<StepSets> &steps,
-                                  int from) {
+                                  int from, bool latest_first = false) {
     std::map<int, int> use;
-    for (int e : edges) use[e] = 1 << 30;
-    for (int i = (int)steps.size() - 1; i >= from; --i)
-        for (int e : steps[(size_t)i].K)
-            if (use.count(e)) use[e] = i;
+    for (int e : edges) use[e] = next_use(e, steps, from);
     std::sort(edges.begin(), edges.end(), [&](int a, int b) {
-        if (use[a] != use[b]) return use[a] < use[b];
+        if (use[a] != use[b]) return latest_first ? use[a] > use[b] : use[a] < use[b];
         return a < b;
     });
     return edges;
@@ -58,13 +63,13 @@ void fill_tables(DevStep &st, const std::vector<int> &lam_in, const std::vector<
     for (int kk = 0; kk < 16; ++kk) {
         int o = 0;
         for (int b = 0; b < st.k; ++b)
-            if ((kk >> b) & 1) o += 1 << pos_of(lam_in, K[(size_t)b]);
+            if ((kk >> b) & 1) o ^= tile_swizzle(1 << pos_of(lam_in, K[(size_t)b]));
         st.koff[kk] = (kk < (1 << st.k)) ? o : 0;
     }
     for (int nn = 0; nn < 16; ++nn) {
         int o = 0;
         for (int b = 0; b < st.n; ++b)
-            if ((nn >> b) & 1) o += 1 << pos_of(lam_out, N[(size_t)b]);
+            if ((nn >> b) & 1) o ^= tile_swizzle(1 << pos_of(lam_out, N[(size_t)b]));
         st.noff[nn] = (nn < (1 << st.n)) ? o : 0;
     }
     for (int half = 0; half < 2; ++half) {
@@ -76,8 +81,8 @@ void fill_tables(DevStep &st, const std::vector<int> &lam_in, const std::vector<
                 int pi = pos_of(lam_in, rest[(size_t)rb]);
                 int po = pos_of(lam_out, rest[(size_t)rb]);
                 if (pi < 0 || po < 0) fail(TN_ERR_UNSUPPORTED, "internal: rest edge lost");
-                oi += 1 << pi;
-                oo += 1 << po;
+                oi ^= tile_swizzle(1 << pi);
+                oo ^= tile_swizzle(1 << po);
             }
             if (half == 0) {
                 st.in_lo[v] = oi;
@@ -109,6 +114,9 @@ DevPass build_pass(const std::vector<int> &Lin, const std::vector<int> &Lout, in
         if (tile_in_edges.count(e)) lam_in.push_back(e);
     P.t_in = (int)lam_in.size();
     // evolve the tile through the group
+    // Intermediate tile states are ordered latest-next-use first: bits that
+    // stay uncontracted occupy the low tile positions, so each step's rest
+    // index (one per thread) walks contiguous, conflict-free positions.
     std::vector<std::vector<int>> lams{lam_in};
     std::vector<int> cur = lam_in;
     for (int s : group) {
@@ -118,6 +126,7 @@ DevPass build_pass(const std::vector<int> &Lin, const std::vector<int> &Lout, in
                 steps[(size_t)s].K.end())
                 nxt.push_back(e);
         for (int e : steps[(size_t)s].N) nxt.push_back(e);
+        nxt = sort_by_next_use(nxt, steps, s + 1, true);
         lams.push_back(nxt);
         cur = nxt;
     }
@@ -230,21 +239,27 @@ void validate_pass(const DevPass &P, const std::vector<int> &chunks) {
         const int t2 = S.rest + S.n;
         if ((1 << t) > P.tile_max || (1 << t2) > P.tile_max) bad("tile size");
         uint64_t mi = 0, mo = 0;
+        // undo the swizzle: tile_swizzle is an involution on single bits' images
+        auto unswz = [](int v) {
+            for (int p = 0; p < 16; ++p)
+                if (tile_swizzle(1 << p) == v) return 1 << p;
+            return -1;
+        };
         for (int b = 0; b < S.rest; ++b) {
-            int vi = b < 6 ? S.in_lo[1 << b] : S.in_hi[1 << (b - 6)];
-            int vo = b < 6 ? S.out_lo[1 << b] : S.out_hi[1 << (b - 6)];
+            int vi = unswz(b < 6 ? S.in_lo[1 << b] : S.in_hi[1 << (b - 6)]);
+            int vo = unswz(b < 6 ? S.out_lo[1 << b] : S.out_hi[1 << (b - 6)]);
             if (vi <= 0 || (vi & (vi - 1)) || (mi & (uint64_t)vi)) bad("rest in offset");
             if (vo <= 0 || (vo & (vo - 1)) || (mo & (uint64_t)vo)) bad("rest out offset");
             mi |= (uint64_t)vi;
             mo |= (uint64_t)vo;
         }
         for (int b = 0; b < S.k; ++b) {
-            int v = S.koff[1 << b];
+            int v = unswz(S.koff[1 << b]);
             if (v <= 0 || (v & (v - 1)) || (mi & (uint64_t)v)) bad("kappa offset");
             mi |= (uint64_t)v;
         }
         for (int b = 0; b < S.n; ++b) {
-            int v = S.noff[1 << b];
+            int v = unswz(S.noff[1 << b]);
             if (v <= 0 || (v & (v - 1)) || (mo & (uint64_t)v)) bad("nu offset");
             mo |= (uint64_t)v;
         }
@@ -259,7 +274,7 @@ void validate_pass(const DevPass &P, const std::vector<int> &chunks) {
 
 BuiltStem build_stem_plan(const Network &net, const Scheme &s, const tn_plan_opts &o) {
     BuiltStem R;
-    const int T_MAX = (o.tile_bits > 0) ? std::min(o.tile_bits, MAX_TILE_BITS) : 11;
+    const int T_MAX = (o.tile_bits > 0) ? std::min(o.tile_bits, MAX_TILE_BITS) : 12;
     const int C_BITS = 4;
     const int max_steps = (o.max_pass_steps > 0) ? std::min(o.max_pass_steps, MAX_PASS_STEPS) : 6;
     const int gemm_min = (o.gemm_min_kn > 0) ? o.gemm_min_kn : 5;
@@ -496,7 +511,9 @@ BuiltStem build_stem_plan(const Network &net, const Scheme &s, const tn_plan_opt
             }
             int next = group.empty() ? i : group.back() + 1;
             std::vector<int> tile_out(cur.begin(), cur.end());
-            tile_out = sort_by_next_use(tile_out, steps, next);
+            // carriers: the contiguous low output bits are the tile-out bits used
+            // last, so the next pass can keep them at its low tile positions
+            tile_out = sort_by_next_use(tile_out, steps, next, true);
             int c_out = std::min(C_BITS, (int)tile_out.size());
             std::vector<int> low(tile_out.begin(), tile_out.begin() + c_out);
             std::vector<int> others;

@@ -213,11 +213,14 @@ def test_grid5x6_m14_against_stored_statevector():
 # sees only structure, so the plan and every launch are the full-size ones)
 # but its value factorises over qubits: a partial amplitude is the product
 # over qubits of <x_q| ... P_v ... |0>, the projectors P_v sitting on the
-# sliced wire segments of that qubit.
+# sliced wire segments of that qubit. Single-qubit sequences made only of
+# sqrt(X) and sqrt(Y) end in exact basis states, so a factor can be zero up to
+# rounding; the test therefore picks, per closed qubit, the prefix bit with the
+# larger factor, and measures the error against the product of the per-qubit
+# vector norms (the scale the FP32 rounding is relative to).
 
-def _closed_form(c, oq, closed_bits, sliced_by_wire, slice_id):
+def _qubit_vectors(c, sliced_by_wire, slice_id):
     n = c.n_qubits
-    # per-qubit list of gate matrices in time order (identity for 2q gates)
     events = [[] for _ in range(n)]
     for t in range(c.n_cycles + 1):
         for q in range(n):
@@ -227,40 +230,55 @@ def _closed_form(c, oq, closed_bits, sliced_by_wire, slice_id):
         for (a, b) in c.pairs[t]:
             events[a].append(np.eye(2))
             events[b].append(np.eye(2))
-    closed = [q for q in range(n) if q not in set(oq)]
     vec = {}
     for q in range(n):
         v = np.array([1.0, 0.0], dtype=complex)
         for s_idx, G in enumerate(events[q]):
             key = (q, s_idx)
             if key in sliced_by_wire:
-                bit = (slice_id >> sliced_by_wire[key]) & 1
-                v = v * (np.arange(2) == bit)
+                v = v * (np.arange(2) == ((slice_id >> sliced_by_wire[key]) & 1))
             v = G @ v
         key = (q, len(events[q]))
         if key in sliced_by_wire:
-            bit = (slice_id >> sliced_by_wire[key]) & 1
-            v = v * (np.arange(2) == bit)
+            v = v * (np.arange(2) == ((slice_id >> sliced_by_wire[key]) & 1))
         vec[q] = v
+    return vec
+
+
+ZERO = 1e-9  # a per-qubit factor below this is zero up to FP64 rounding
+
+
+def _closed_form(c, oq, closed_bits, sliced_by_wire, slice_id):
+    """Partial amplitudes and their scale: the product of the per-qubit
+    factors' magnitudes with numerically-zero factors counted as 1 (the FP32
+    rounding of such a factor is relative to its unit-norm chain)."""
+    vec = _qubit_vectors(c, sliced_by_wire, slice_id)
+    closed = [q for q in range(c.n_qubits) if q not in set(oq)]
     scal = 1.0 + 0j
+    scale = 1.0
     for q, b in zip(closed, closed_bits):
-        scal *= vec[q][int(b)]
+        f = vec[q][int(b)]
+        scal *= f
+        scale *= abs(f) if abs(f) > ZERO else 1.0
     out = np.ones(1, dtype=complex)
     for q in oq:
         out = np.kron(out, vec[q])
-    return scal * out
+        nv = np.linalg.norm(vec[q])
+        scale *= nv if nv > ZERO else 1.0
+    return scal * out, scale
 
 
 @pytest.mark.parametrize("name", ["diag53_m14", "diag53_m12"])
 def test_full_size_plan_identity_fsim_closed_form(name):
-    from bench import plan_options
+    from bench import plan_options, workload_inputs
     cfg = CONFIGS[name]
-    c = config_circuit(name)
+    c, oq, cb_bench = workload_inputs(name)
     c0 = Circuit(c.n_qubits, c.n_cycles, c.gates_1q, c.pairs, 0.0, 0.0, c.layout)
-    oq = c.layout.open_qubits(cfg["n_open"])
-    cb = list(random_bits(c.n_qubits - len(oq), cfg["bit_seed"]))
+    closed = [q for q in range(c.n_qubits) if q not in set(oq)]
+    v0 = _qubit_vectors(c0, {}, 0)
+    cb = [int(np.argmax(np.abs(v0[q]))) for q in closed]
     opts = plan_options(name)
-    net_ref, plan_ref = _plan(c, oq, cb, **opts)
+    net_ref, plan_ref = _plan(c, oq, cb_bench, **opts)
     net, plan = _plan(c0, oq, cb, **opts)
     o1, s1 = P.tn_plan_export(plan_ref)
     o2, s2 = P.tn_plan_export(plan)
@@ -270,16 +288,17 @@ def test_full_size_plan_identity_fsim_closed_form(name):
     _, _, q, s = net.info()
     wires = {(int(q[e]), int(s[e])): j for j, e in enumerate(s2)}
     nsl = info["n_sliced"]
-    ids = [0, 1, (1 << nsl) - 1, 12345 % (1 << nsl)]
+    ids = [0, 1, 2, (1 << nsl) - 1, 12345 % (1 << nsl), 987654 % (1 << nsl)]
     for sid in ids:
         got = run(plan, sid, sid + 1)[0]
-        ref = _closed_form(c0, oq, cb, wires, sid)
-        if np.linalg.norm(ref) > 1e-30:
+        ref, scale = _closed_form(c0, oq, cb, wires, sid)
+        err = np.linalg.norm(got - ref) / scale
+        assert err < TOL, (sid, err)
+        if np.linalg.norm(ref) > 1e-2 * scale:
             assert rel_l2(got, ref) < TOL, (sid, rel_l2(got, ref))
-        else:
-            assert np.linalg.norm(got) <= 1e-6 * (2.0 ** (-c.n_qubits / 2))
     # a whole batch at the bench's batch size
     sb = info["batch_items"]
     got = run(plan, 0, sb)[0]
-    ref = sum(_closed_form(c0, oq, cb, wires, sid) for sid in range(sb))
-    assert rel_l2(got, ref) < TOL
+    parts = [_closed_form(c0, oq, cb, wires, sid) for sid in range(sb)]
+    ref = sum(p[0] for p in parts)
+    assert np.linalg.norm(got - ref) / max(p[1] for p in parts) < TOL
