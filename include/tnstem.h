@@ -190,6 +190,25 @@ tn_status tn_plan_profile(tn_plan *plan, uint64_t slice_begin, tn_precision prec
                           tn_exec_mode mode, void *cuda_stream, tn_launch_record *out,
                           int32_t max_records, int32_t *n_records);
 
+/* Allocation-free variant of tn_contract_stem (fused mode, FP32). The paper
+ * has no counterpart; this exists for callers that must not allocate device
+ * memory while contracting: cudaMalloc synchronises the device and can fail
+ * under a memory budget owned by someone else (a framework's pooling
+ * allocator, a GPU shared under a fixed quota). Scratch lives in one static
+ * device array of the library (two stem buffers of 2^20 complex64 entries and
+ * 2^14 compensated FP64 sums, about 16.5 MiB held on every GPU that loads the
+ * library until exit). Requirements: the plan is prepared (tn_plan_prepare
+ * allocates; this call does not), n_prefixes * 2^max_rank <= 2^20 and
+ * n_prefixes * 2^n_open <= 2^14, else TN_ERR_UNSUPPORTED; amps_out is device
+ * memory (else TN_ERR_INVALID_ARG). Arguments and result are as for
+ * tn_contract_stem. The first call on each device looks up the array's
+ * address (cudaGetSymbolAddress) and must come before any stream capture on
+ * the calling thread. All calls share the array and each clears the sums it
+ * uses first; calls that overlap on the GPU race, so serialise them.
+ * Asynchronous on cuda_stream. */
+tn_status tn_contract_stem_noalloc(tn_plan *plan, uint64_t slice_begin, uint64_t slice_end,
+                                   void *cuda_stream, double *amps_out, int32_t accumulate);
+
 void tn_plan_destroy(tn_plan *plan);
 void tn_network_destroy(tn_network *net);
 

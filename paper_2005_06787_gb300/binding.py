@@ -26,7 +26,8 @@ MODE = {"plain": 0, "fused": 1}
 
 EXPORTED = [
     "tn_build_network", "tn_network_info", "tn_plan_create", "tn_plan_prepare", "tn_plan_info",
-    "tn_plan_export", "tn_plan_steps", "tn_contract_stem", "tn_plan_profile", "tn_plan_destroy",
+    "tn_plan_export", "tn_plan_steps", "tn_contract_stem", "tn_contract_stem_noalloc",
+    "tn_plan_profile", "tn_plan_destroy",
     "tn_network_destroy", "tn_linear_xeb", "tn_permute", "tn_cgemm", "tn_last_error",
     "tn_version",
 ]
@@ -95,6 +96,7 @@ def load():
     L.tn_plan_export.argtypes = [vp, vp, vp]
     L.tn_plan_steps.argtypes = [vp, vp, i32, vp]
     L.tn_contract_stem.argtypes = [vp, u64, u64, C.c_int, C.c_int, vp, vp, i32]
+    L.tn_contract_stem_noalloc.argtypes = [vp, u64, u64, vp, vp, i32]
     L.tn_plan_destroy.argtypes = [vp]
     L.tn_plan_destroy.restype = None
     L.tn_network_destroy.argtypes = [vp]
@@ -272,6 +274,15 @@ def tn_contract_stem(plan: Plan, slice_begin: int, slice_end: int, out, prec: st
     L = load()
     _check(L.tn_contract_stem(plan.handle, int(slice_begin), int(slice_end), PREC[prec],
                               MODE[mode], _stream(stream), _ptr(out), int(bool(accumulate))))
+    return out
+
+
+def tn_contract_stem_noalloc(plan: Plan, slice_begin: int, slice_end: int, out, stream=None,
+                             accumulate: bool = False):
+    """Allocation-free fused contraction; out must be a CUDA float64 tensor."""
+    L = load()
+    _check(L.tn_contract_stem_noalloc(plan.handle, int(slice_begin), int(slice_end),
+                                      _stream(stream), _ptr(out), int(bool(accumulate))))
     return out
 
 

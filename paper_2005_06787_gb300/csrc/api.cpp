@@ -219,6 +219,15 @@ tn_status tn_plan_profile(tn_plan *plan, uint64_t slice_begin, tn_precision prec
     });
 }
 
+tn_status tn_contract_stem_noalloc(tn_plan *plan, uint64_t slice_begin, uint64_t slice_end,
+                                   void *cuda_stream, double *amps_out, int32_t accumulate) {
+    return guard([&] {
+        if (!plan) tn::fail(TN_ERR_INVALID_ARG, "null plan");
+        tn::plan_contract_noalloc(*plan->p, slice_begin, slice_end, (cudaStream_t)cuda_stream,
+                                  amps_out, accumulate);
+    });
+}
+
 void tn_plan_destroy(tn_plan *plan) { delete plan; }
 void tn_network_destroy(tn_network *net) { delete net; }
 

@@ -52,6 +52,8 @@ struct Plan {
 void plan_prepare(Plan &p, const uint8_t *prefixes, int n_prefixes, cudaStream_t st);
 std::vector<tn_launch_record> plan_profile(Plan &p, uint64_t s0, tn_precision prec,
                                           tn_exec_mode mode, cudaStream_t st);
+void plan_contract_noalloc(Plan &p, uint64_t s0, uint64_t s1, cudaStream_t st, double *amps_out,
+                           int accumulate);
 void plan_contract(Plan &p, uint64_t s0, uint64_t s1, tn_precision prec, tn_exec_mode mode,
                    cudaStream_t st, double *amps_out, int accumulate);
 
