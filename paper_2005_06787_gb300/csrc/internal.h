@@ -3,12 +3,13 @@
 #pragma once
 
 #include <complex>
+#include <cstddef>
 #include <cstdint>
 #include <random>
 #include <string>
 #include <vector>
 
-#include "../../include/tnstem.h"
+#include "tnstem.h"
 
 namespace tn {
 
@@ -170,7 +171,7 @@ std::vector<std::pair<int, int>> export_order(const Network &net, const Scheme &
 
 // ----------------------------------------------------------------- device plan
 constexpr int MAX_PASS_STEPS = 8;
-constexpr int MAX_STEP_K = 4;    // k, n <= 4 inside fused passes
+constexpr int MAX_STEP_K = 4;    // k + n <= 4 inside fused passes
 constexpr int MAX_TILE_BITS = 12;
 constexpr int MAX_BRANCH_SLICED = 24;
 constexpr int MAX_FREE = 40;
@@ -186,7 +187,7 @@ inline int tile_swizzle(int p) {
 }
 
 // All offsets are in complex elements; tile offsets are swizzled positions.
-struct DevStep {
+struct alignas(16) DevStep {
     int k, n, rest;
     int branch;                 // index into DevBranch table
     int koff[16], noff[16];     // tile offsets of kappa / nu bits
@@ -219,6 +220,8 @@ struct alignas(16) DevPass {
     DevStep steps[MAX_PASS_STEPS];
 };
 static_assert(sizeof(DevPass) % 16 == 0, "DevPass must be a multiple of 16 bytes");
+static_assert(sizeof(DevStep) % 16 == 0, "DevStep must be a multiple of 16 bytes");
+static_assert(offsetof(DevPass, steps) % 16 == 0, "DevPass steps must start 16-byte aligned");
 
 // Host-side description of the executable stem.
 struct ExecStep {  // plain mode: permute pass + GEMM

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstddef>
 #include <cstdint>
 
 #include "kernels.h"
@@ -38,51 +39,50 @@ __device__ __forceinline__ int dev_swizzle(int p) {
 // One stem step inside the tile: for each rest index rho (thread-strided),
 // y[nu] = sum_kappa x[kappa] * B[kappa][nu], read at in-tile offsets
 // io(rho) + koff[kappa], written at oo(rho) + noff[nu].
+// One stem step on the tile: for each rest index rho (one per thread and
+// iteration), y[nu] = sum_kappa x[kappa] * B[kappa][nu], read at in-tile
+// offsets io(rho) ^ koff[kappa], written at oo(rho) ^ noff[nu]. Branch
+// clusters have rank <= 4, so B (2^(K+N) <= 16 entries) and both offset lists
+// live in registers for the whole step. The thread count is a power of two
+// >= 64, so the low six bits of rho are fixed per thread and only the high
+// half of each offset table is read per iteration.
 template <int K, int N>
 __device__ __forceinline__ void step_body(const float2 *__restrict__ tin, float2 *__restrict__ tout,
                                           const DevStep &S, const float2 *__restrict__ Bm, int nt) {
     constexpr int NK = 1 << K, NN = 1 << N;
-    int koff[NK];
+    float2 bv[NK * NN];
+#pragma unroll
+    for (int i = 0; i < NK * NN; ++i) bv[i] = Bm[i];
+    int koff[NK], noff[NN];
 #pragma unroll
     for (int kk = 0; kk < NK; ++kk) koff[kk] = S.koff[kk];
+#pragma unroll
+    for (int nn = 0; nn < NN; ++nn) noff[nn] = S.noff[nn];
     const int nrest = 1 << S.rest;
+    const int io_lo = S.in_lo[threadIdx.x & 63], oo_lo = S.out_lo[threadIdx.x & 63];
     for (int r = threadIdx.x; r < nrest; r += nt) {
-        const int io = S.in_lo[r & 63] ^ S.in_hi[r >> 6];
-        const int oo = S.out_lo[r & 63] ^ S.out_hi[r >> 6];
+        const int io = io_lo ^ S.in_hi[r >> 6];
+        const int oo = oo_lo ^ S.out_hi[r >> 6];
         float2 x[NK];
 #pragma unroll
         for (int kk = 0; kk < NK; ++kk) x[kk] = tin[io ^ koff[kk]];
-        if constexpr (NN == 1) {
+#pragma unroll
+        for (int nn = 0; nn < NN; ++nn) {
             float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int kk = 0; kk < NK; ++kk) cfma(acc, x[kk], Bm[kk]);
-            tout[oo ^ S.noff[0]] = acc;
-        } else {
-            // two outputs per iteration; B[kappa][nu], B[kappa][nu+1] in one 16-byte load
-#pragma unroll 1
-            for (int nn = 0; nn < NN; nn += 2) {
-                float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
-#pragma unroll
-                for (int kk = 0; kk < NK; ++kk) {
-                    const float4 b = *reinterpret_cast<const float4 *>(Bm + kk * NN + nn);
-                    cfma(a0, x[kk], make_float2(b.x, b.y));
-                    cfma(a1, x[kk], make_float2(b.z, b.w));
-                }
-                tout[oo ^ S.noff[nn]] = a0;
-                tout[oo ^ S.noff[nn + 1]] = a1;
-            }
+            for (int kk = 0; kk < NK; ++kk) cfma(acc, x[kk], bv[kk * NN + nn]);
+            tout[oo ^ noff[nn]] = acc;
         }
     }
 }
 
+// Identity step of a pure permutation pass.
 __device__ __forceinline__ void copy_body(const float2 *__restrict__ tin, float2 *__restrict__ tout,
                                           const DevStep &S, int nt) {
     const int nrest = 1 << S.rest;
-    for (int r = threadIdx.x; r < nrest; r += nt) {
-        const int io = S.in_lo[r & 63] ^ S.in_hi[r >> 6];
-        const int oo = S.out_lo[r & 63] ^ S.out_hi[r >> 6];
-        tout[oo] = tin[io];
-    }
+    const int io_lo = S.in_lo[threadIdx.x & 63], oo_lo = S.out_lo[threadIdx.x & 63];
+    for (int r = threadIdx.x; r < nrest; r += nt)
+        tout[oo_lo ^ S.out_hi[r >> 6]] = tin[io_lo ^ S.in_hi[r >> 6]];
 }
 
 __device__ void run_step(const float2 *tin, float2 *tout, const DevStep &S, const float2 *Bm,
@@ -94,35 +94,47 @@ __device__ void run_step(const float2 *tin, float2 *tout, const DevStep &S, cons
     switch (S.k * 8 + S.n) {
 #define TN_CASE(K, N) \
     case K * 8 + N: step_body<K, N>(tin, tout, S, Bm, nt); break;
-        TN_CASE(1, 0) TN_CASE(1, 1) TN_CASE(1, 2) TN_CASE(1, 3) TN_CASE(1, 4)
-        TN_CASE(2, 0) TN_CASE(2, 1) TN_CASE(2, 2) TN_CASE(2, 3) TN_CASE(2, 4)
-        TN_CASE(3, 0) TN_CASE(3, 1) TN_CASE(3, 2) TN_CASE(3, 3) TN_CASE(3, 4)
-        TN_CASE(4, 0) TN_CASE(4, 1) TN_CASE(4, 2) TN_CASE(4, 3) TN_CASE(4, 4)
+        TN_CASE(1, 0) TN_CASE(1, 1) TN_CASE(1, 2) TN_CASE(1, 3)
+        TN_CASE(2, 0) TN_CASE(2, 1) TN_CASE(2, 2)
+        TN_CASE(3, 0) TN_CASE(3, 1)
+        TN_CASE(4, 0)
 #undef TN_CASE
         default: break;
     }
 }
 
 constexpr int PASS_THREADS = 256;
+constexpr size_t PASS_HEAD_BYTES = (offsetof(DevPass, steps) + 15) / 16 * 16;
 
-
-__global__ void __launch_bounds__(PASS_THREADS)
+// A fused pass over batch items x tiles, one tile per block iteration: load
+// the tile (16-byte loads of contiguous chunks, swizzled into shared memory),
+// apply the pass's stem steps, store the tile in the next layout.
+// Shared memory: pass header and used step tables | chunk tables | two tiles
+// | branch matrices of the current batch item.
+template <int MINB>
+__global__ void __launch_bounds__(PASS_THREADS, MINB)
 pass_kernel(const DevPass *__restrict__ gpass, const int *__restrict__ chunks,
             const DevBranch *__restrict__ branches, const float2 *__restrict__ pool,
             const float2 *__restrict__ in, float2 *__restrict__ out, BatchArgs ba) {
     extern __shared__ __align__(16) unsigned char smem[];
     DevPass &P = *reinterpret_cast<DevPass *>(smem);
+    const int n_steps_g = gpass->n_steps;
     {
         const int4 *src = reinterpret_cast<const int4 *>(gpass);
         int4 *dst = reinterpret_cast<int4 *>(smem);
-        for (int i = threadIdx.x; i < (int)(sizeof(DevPass) / 16); i += PASS_THREADS) dst[i] = src[i];
+        const int n16 = (int)((PASS_HEAD_BYTES + (size_t)n_steps_g * sizeof(DevStep)) / 16);
+        for (int i = threadIdx.x; i < n16; i += PASS_THREADS) dst[i] = src[i];
     }
     __syncthreads();
-    constexpr size_t PASS_BYTES = (sizeof(DevPass) + 15) / 16 * 16;
-    float2 *tA = reinterpret_cast<float2 *>(smem + PASS_BYTES);
+    const size_t head = PASS_HEAD_BYTES + (size_t)P.n_steps * sizeof(DevStep);
+    int *cin_tab = reinterpret_cast<int *>(smem + head);
+    const int n_cin = 1 << (P.t_in - P.c_in), n_cout = 1 << (P.t_out - P.c_out);
+    int *cout_tab = cin_tab + n_cin;
+    float2 *tA = reinterpret_cast<float2 *>(smem + head + (size_t)((n_cin + n_cout + 3) & ~3) * 4);
     float2 *tB = tA + P.tile_max;
     float2 *bm = tB + P.tile_max;
-    // branch matrices of the pass's steps sit back to back after the tiles
+    for (int i = threadIdx.x; i < n_cin; i += PASS_THREADS) cin_tab[i] = chunks[P.chunk_in_base + i];
+    for (int i = threadIdx.x; i < n_cout; i += PASS_THREADS) cout_tab[i] = chunks[P.chunk_out_base + i];
     auto bm_off = [&](int t) {
         int o = 0;
         for (int u = 0; u < t; ++u)
@@ -133,52 +145,53 @@ pass_kernel(const DevPass *__restrict__ gpass, const int *__restrict__ chunks,
     const int64_t base = ba.state->slice_base;
     const int64_t send = ba.state->slice_end;
     const int tin_n = 1 << P.t_in, tout_n = 1 << P.t_out;
-    const int cin_mask = (1 << P.c_in) - 1, cout_mask = (1 << P.c_out) - 1;
-    const int *cin_tab = chunks + P.chunk_in_base;
-    const int *cout_tab = chunks + P.chunk_out_base;
-    int64_t last_item = -1;
+    const int c_in = P.c_in, c_out = P.c_out;
+    const int cin_mask = (1 << c_in) - 1, cout_mask = (1 << c_out) - 1;
+    const int nfree = P.n_free;
+    const unsigned lane = threadIdx.x & 31;
+    // this lane's free bit (free bits are disjoint, so offsets combine with OR)
+    const unsigned my_fin = lane < (unsigned)nfree ? (unsigned)P.free_in[lane] : 0u;
+    const unsigned my_fout = lane < (unsigned)nfree ? (unsigned)P.free_out[lane] : 0u;
+    __syncthreads();
+    int last_item = -1;
     for (int64_t u = blockIdx.x; u < n_units; u += gridDim.x) {
-        const int64_t item = u >> P.n_free;
-        const int64_t tile = u & (P.n_tiles - 1);
-        const int pl = (int)(item / ba.SB);
+        const int item = (int)(u >> nfree);
+        const unsigned tile = (unsigned)(u & (P.n_tiles - 1));
+        const int pl = item / ba.SB;
         const int p = ba.p0 + pl;
-        const int64_t s = base + (item - (int64_t)pl * ba.SB);
+        const int64_t s = base + (item - pl * ba.SB);
         if (s >= send) continue;  // uniform over the block
         if (item != last_item) {
             for (int t = 0; t < P.n_steps; ++t) {
                 const int br = P.steps[t].branch;
                 if (br < 0) continue;
-                const DevBranch &b = branches[br];
-                const float2 *src = pool + branch_offset(b, p, s);
+                const float2 *bsrc = pool + branch_offset(branches[br], p, s);
                 const int cnt = 1 << (P.steps[t].k + P.steps[t].n);
                 const int bo = bm_off(t);
-                for (int i = threadIdx.x; i < cnt; i += PASS_THREADS) bm[bo + i] = src[i];
+                for (int i = threadIdx.x; i < cnt; i += PASS_THREADS) bm[bo + i] = bsrc[i];
             }
             last_item = item;
         }
-        int64_t ib = 0, ob = 0;
-        for (int f = 0; f < P.n_free; ++f)
-            if ((tile >> f) & 1) {
-                ib += P.free_in[f];
-                ob += P.free_out[f];
-            }
+        const bool mine = (tile >> lane) & 1u;
+        const unsigned ib = __reduce_or_sync(0xffffffffu, mine ? my_fin : 0u);
+        const unsigned ob = __reduce_or_sync(0xffffffffu, mine ? my_fout : 0u);
         const float2 *src;
         if (P.in_branch >= 0)
             src = pool + branch_offset(branches[P.in_branch], p, s);
         else
-            src = in + item * P.in_item_stride;
-        float2 *dst = out + item * P.out_item_stride;
-        // load tile: tile-local index = chunk * 2^c_in + w
-        if (P.c_in >= 1) {
+            src = in + (int64_t)item * P.in_item_stride;
+        src += ib;
+        float2 *dst = out + (int64_t)item * P.out_item_stride + ob;
+        if (c_in >= 1) {
             for (int idx = threadIdx.x * 2; idx < tin_n; idx += PASS_THREADS * 2) {
-                const int j = idx >> P.c_in, w = idx & cin_mask;
-                const float4 v = *reinterpret_cast<const float4 *>(src + ib + cin_tab[j] + w);
-                tA[dev_swizzle(idx)] = make_float2(v.x, v.y);
-                tA[dev_swizzle(idx + 1)] = make_float2(v.z, v.w);
+                const float4 v = *reinterpret_cast<const float4 *>(src + cin_tab[idx >> c_in] + (idx & cin_mask));
+                const int ph = dev_swizzle(idx);
+                tA[ph] = make_float2(v.x, v.y);
+                tA[ph ^ 1] = make_float2(v.z, v.w);
             }
         } else {
             for (int idx = threadIdx.x; idx < tin_n; idx += PASS_THREADS)
-                tA[dev_swizzle(idx)] = src[ib + cin_tab[idx]];
+                tA[dev_swizzle(idx)] = src[cin_tab[idx]];
         }
         __syncthreads();
         float2 *cur = tA, *nxt = tB;
@@ -189,22 +202,24 @@ pass_kernel(const DevPass *__restrict__ gpass, const int *__restrict__ chunks,
             cur = nxt;
             nxt = tmp;
         }
-        if (P.c_out >= 1) {
+        if (c_out >= 1) {
             for (int idx = threadIdx.x * 2; idx < tout_n; idx += PASS_THREADS * 2) {
-                const int j = idx >> P.c_out, w = idx & cout_mask;
-                const float2 a = cur[dev_swizzle(idx)], b = cur[dev_swizzle(idx + 1)];
-                *reinterpret_cast<float4 *>(dst + ob + cout_tab[j] + w) = make_float4(a.x, a.y, b.x, b.y);
+                const int ph = dev_swizzle(idx);
+                const float2 a = cur[ph], b = cur[ph ^ 1];
+                *reinterpret_cast<float4 *>(dst + cout_tab[idx >> c_out] + (idx & cout_mask)) =
+                    make_float4(a.x, a.y, b.x, b.y);
             }
         } else {
             for (int idx = threadIdx.x; idx < tout_n; idx += PASS_THREADS)
-                dst[ob + cout_tab[idx]] = cur[dev_swizzle(idx)];
+                dst[cout_tab[idx]] = cur[dev_swizzle(idx)];
         }
         __syncthreads();
     }
 }
 
 static size_t pass_smem_bytes(const DevPass &P) {
-    size_t b = (sizeof(DevPass) + 15) / 16 * 16;
+    size_t b = PASS_HEAD_BYTES + (size_t)P.n_steps * sizeof(DevStep);
+    b += (size_t)((((1 << (P.t_in - P.c_in)) + (1 << (P.t_out - P.c_out))) + 3) & ~3) * 4;
     b += 2 * (size_t)P.tile_max * sizeof(float2);
     for (int t = 0; t < P.n_steps; ++t)
         if (P.steps[t].branch >= 0) b += ((size_t)1 << (P.steps[t].k + P.steps[t].n)) * sizeof(float2);
@@ -223,14 +238,26 @@ cudaError_t launch_pass(const DevPass *d_pass, const DevPass &h_pass, const int 
         cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
     }
     const size_t smem = pass_smem_bytes(h_pass);
+    // three blocks per SM (registers capped at 80) measured faster than two
+    // blocks with 96 registers; the 96-register variant is used only when the
+    // tile's shared memory does not fit three blocks
     int occ = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pass_kernel, PASS_THREADS, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pass_kernel<3>, PASS_THREADS, smem);
     if (e != cudaSuccess) return e;
+    const bool small_tile = occ >= 3;
+    if (!small_tile) {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pass_kernel<2>, PASS_THREADS, smem);
+        if (e != cudaSuccess) return e;
+    }
     if (occ < 1) return cudaErrorInvalidConfiguration;
     const int64_t units = (int64_t)ba.n_items * h_pass.n_tiles;
     const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(units, (int64_t)num_sms * occ));
-    pass_kernel<<<(unsigned)grid, PASS_THREADS, smem, st>>>(d_pass, d_chunks, d_branches, pool, in,
-                                                            out, ba);
+    if (small_tile)
+        pass_kernel<3><<<(unsigned)grid, PASS_THREADS, smem, st>>>(d_pass, d_chunks, d_branches, pool,
+                                                                   in, out, ba);
+    else
+        pass_kernel<2><<<(unsigned)grid, PASS_THREADS, smem, st>>>(d_pass, d_chunks, d_branches, pool,
+                                                                   in, out, ba);
     return cudaGetLastError();
 }
 
@@ -530,8 +557,10 @@ cudaError_t launch_permute(const float2 *in, float2 *out, int rank, const int *d
 
 // Raise the dynamic shared-memory limits once, outside any stream capture.
 cudaError_t init_kernels() {
-    cudaError_t e = cudaFuncSetAttribute(pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(pass_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          200 * 1024);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(pass_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(cgemm_simt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 96 * 1024);

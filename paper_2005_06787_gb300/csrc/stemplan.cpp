@@ -30,6 +30,13 @@ int pos_of(const std::vector<int> &layout, int e) {
     return -1;
 }
 
+// Steps the fused pass kernel applies in shared memory: at least one
+// contracted bit and a branch matrix of at most 2^4 entries (kept in
+// registers); anything else runs as a GEMM step.
+bool fusable_step(int k, int n, int gemm_min) {
+    return k >= 1 && k + n <= MAX_STEP_K && k < gemm_min && n < gemm_min;
+}
+
 // Index of the first step >= from that contracts e (never: 1 << 30).
 int next_use(int e, const std::vector<StepSets> &steps, int from) {
     for (int i = from; i < (int)steps.size(); ++i)
@@ -202,6 +209,7 @@ void validate_pass(const DevPass &P, const std::vector<int> &chunks) {
     if (P.t_in > MAX_TILE_BITS + 1 || P.t_out > MAX_TILE_BITS + 1) bad("tile bits");
     if (P.c_in > P.t_in || P.c_out > P.t_out) bad("chunk bits");
     if (P.n_steps < 1 || P.n_steps > MAX_PASS_STEPS) bad("step count");
+    if (P.n_free > 32) bad("more than 32 free bits");
     auto check_side = [&](int r, int t, int c, int base, const int64_t *free) {
         uint64_t mask = (c > 0) ? ((1ull << c) - 1) : 0;
         int bits = c;
@@ -233,7 +241,8 @@ void validate_pass(const DevPass &P, const std::vector<int> &chunks) {
     int t = P.t_in;
     for (int i = 0; i < P.n_steps; ++i) {
         const DevStep &S = P.steps[i];
-        if (S.k < 0 || S.k > MAX_STEP_K || S.n < 0 || S.n > MAX_STEP_K) bad("step k/n");
+        if (S.k < 0 || S.n < 0 || S.k + S.n > MAX_STEP_K) bad("step k/n");
+        if (S.branch >= 0 && S.k < 1) bad("fused step without contracted bits");
         if (S.branch < 0 && (S.k || S.n)) bad("copy step with k/n");
         if (S.rest != t - S.k || S.rest > 12) bad("rest bits");
         const int t2 = S.rest + S.n;
@@ -268,6 +277,20 @@ void validate_pass(const DevPass &P, const std::vector<int> &chunks) {
     }
     if (t != P.t_out) bad("final tile bits");
     if (P.n_tiles != (1ll << P.n_free)) bad("tile count");
+}
+
+// Tile of a pure permutation: the low c input bits and the low c output bits
+// (both contiguous in their tensors), widened with further input bits up to
+// 2^t_max entries so each block iteration moves a full tile.
+std::set<int> permute_tile(const std::vector<int> &lay, const std::vector<int> &perm_out, int c,
+                           int t_max) {
+    std::set<int> tile;
+    for (int p = 0; p < c; ++p) {
+        tile.insert(lay[(size_t)p]);
+        tile.insert(perm_out[(size_t)p]);
+    }
+    for (size_t p = 0; p < lay.size() && (int)tile.size() < t_max; ++p) tile.insert(lay[p]);
+    return tile;
 }
 
 }  // namespace
@@ -353,11 +376,7 @@ BuiltStem build_stem_plan(const Network &net, const Scheme &s, const tn_plan_opt
                 if (std::find(st.K.begin(), st.K.end(), e) == st.K.end()) perm_out.push_back(e);
             int r = (int)lay.size();
             int c = std::min(C_BITS, r);
-            std::set<int> tile;
-            for (int p = 0; p < c; ++p) {
-                tile.insert(lay[(size_t)p]);
-                tile.insert(perm_out[(size_t)p]);
-            }
+            std::set<int> tile = permute_tile(lay, perm_out, c, std::min(11, T_MAX));
             DevPass P = build_pass(lay, perm_out, c, c, tile, {}, steps, branch_of_step,
                                    R.sp.chunk_table);
             if (i == 0) P.in_branch = s.seed_cluster;
@@ -402,17 +421,13 @@ BuiltStem build_stem_plan(const Network &net, const Scheme &s, const tn_plan_opt
             if (L > 0) {
                 const StepSets &st = steps[(size_t)i];
                 int k = (int)st.K.size(), n = (int)st.N.size();
-                if (k > MAX_STEP_K || n > MAX_STEP_K || k == 0 || k >= gemm_min || n >= gemm_min) {
+                if (!fusable_step(k, n, gemm_min)) {
                     // GEMM step: permute to [K | rest], then GEMM -> [N | rest]
                     std::vector<int> perm_out = st.K;
                     for (int e : lay)
                         if (std::find(st.K.begin(), st.K.end(), e) == st.K.end())
                             perm_out.push_back(e);
-                    std::set<int> tile;
-                    for (int p = 0; p < c_in; ++p) {
-                        tile.insert(lay[(size_t)p]);
-                        tile.insert(perm_out[(size_t)p]);
-                    }
+                    std::set<int> tile = permute_tile(lay, perm_out, c_in, std::min(11, T_MAX));
                     DevPass P = build_pass(lay, perm_out, c_in, c_in, tile, {}, steps,
                                            branch_of_step, R.sp.chunk_table);
                     if (first) P.in_branch = s.seed_cluster;
@@ -442,8 +457,7 @@ BuiltStem build_stem_plan(const Network &net, const Scheme &s, const tn_plan_opt
                 while (j < L && (int)group.size() < max_steps) {
                     const StepSets &st = steps[(size_t)j];
                     int k = (int)st.K.size(), n = (int)st.N.size();
-                    if (k > MAX_STEP_K || n > MAX_STEP_K || k == 0 || k >= gemm_min || n >= gemm_min)
-                        break;
+                    if (!fusable_step(k, n, gemm_min)) break;
                     std::set<int> trial = in_tile;
                     // edges needed from the input: K_j edges that are input edges
                     for (int e : st.K)
@@ -475,11 +489,7 @@ BuiltStem build_stem_plan(const Network &net, const Scheme &s, const tn_plan_opt
                 std::vector<int> perm_out = st.K;
                 for (int e : lay)
                     if (std::find(st.K.begin(), st.K.end(), e) == st.K.end()) perm_out.push_back(e);
-                std::set<int> tile;
-                for (int p = 0; p < c_in; ++p) {
-                    tile.insert(lay[(size_t)p]);
-                    tile.insert(perm_out[(size_t)p]);
-                }
+                std::set<int> tile = permute_tile(lay, perm_out, c_in, std::min(11, T_MAX));
                 DevPass P = build_pass(lay, perm_out, c_in, c_in, tile, {}, steps, branch_of_step,
                                        R.sp.chunk_table);
                 if (first) P.in_branch = s.seed_cluster;
