@@ -426,7 +426,7 @@ cudaError_t launch_stem_gemm(const float2 *A, float2 *C, int64_t M, int k, int n
 cudaError_t launch_cgemm(const float2 *A, const float2 *B, float2 *C, int64_t M, int64_t K,
                          int64_t N, int64_t batch, int64_t sA, int64_t sB, int64_t sC,
                          tn_precision prec, cudaStream_t st) {
-    (void)prec;
+    if (prec != TN_PREC_FP32_SIMT) return launch_tc_cgemm(A, B, C, M, K, N, batch, sA, sB, sC, prec, st);
     GemmItemSrc g{A, C, B, sA, sB, sC, nullptr, nullptr, BatchArgs{nullptr, 1, 0, 0}, 0};
     return run_simt_gemm(g, M, K, N, batch, st);
 }
@@ -561,6 +561,8 @@ cudaError_t init_kernels() {
                                          200 * 1024);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(pass_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    e = tc_gemm_init();
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(cgemm_simt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 96 * 1024);

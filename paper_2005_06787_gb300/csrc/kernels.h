@@ -63,6 +63,11 @@ cudaError_t launch_permute(const float2 *in, float2 *out, int rank, const int *p
                            cudaStream_t st);
 
 bool tc_gemm_supported(int k, int n);
+cudaError_t tc_gemm_init();
+cudaError_t tc_error_flag(int *out);
+cudaError_t launch_tc_cgemm(const float2 *A, const float2 *B, float2 *C, int64_t M, int64_t K,
+                            int64_t N, int64_t batch, int64_t sA, int64_t sB, int64_t sC,
+                            tn_precision prec, cudaStream_t st);
 cudaError_t launch_tc_stem_gemm(const float2 *A, float2 *C, int64_t M, int k, int n,
                                 int64_t strideA, int64_t strideC, const DevBranch *d_branch_entry,
                                 const float2 *pool, BatchArgs ba, tn_precision prec,

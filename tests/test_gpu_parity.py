@@ -84,6 +84,28 @@ def test_cgemm_simt_matches_fp64(M, K, N, batch):
     assert rel_l2(got, ref) < TOL
 
 
+# relative L2 bounds per precision: 3xTF32 carries ~21 mantissa bits per
+# product (gated at the FP32-path tolerance); 3xBF16 ~16 bits; 1xBF16 8 bits
+TC_TOL = {"tf32x3": 1e-5, "bf16x3": 1e-4, "bf16x1": 1e-2}
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3", "bf16x1"])
+@pytest.mark.parametrize("M,K,N,batch", [(128, 16, 8, 1), (1000, 4, 8, 1), (4096, 16, 16, 2),
+                                         (777, 64, 64, 1), (333, 3, 5, 3), (300, 128, 128, 1),
+                                         (256, 32, 200, 1), (1, 1, 1, 1)])
+def test_cgemm_tensor_core_matches_fp64(prec, M, K, N, batch):
+    A = random_complex((batch, M, K), 21, np.complex64)
+    B = random_complex((batch, K, N), 22, np.complex64)
+    dA = torch.from_numpy(A.view(np.float32).copy()).cuda()
+    dB = torch.from_numpy(B.view(np.float32).copy()).cuda()
+    dC = torch.full((batch * M * N * 2,), float("nan"), dtype=torch.float32, device="cuda")
+    P.tn_cgemm(dA, dB, dC, M, K, N, batch, M * K, K * N, M * N, prec=prec)
+    torch.cuda.synchronize()
+    got = dC.cpu().numpy().view(np.complex64).reshape(batch, M, N)
+    ref = np.matmul(A.astype(np.complex128), B.astype(np.complex128))
+    assert rel_l2(got, ref) < TC_TOL[prec], rel_l2(got, ref)
+
+
 def test_linear_xeb_kernel():
     a = random_complex((4096,), 3) / 64.0
     d = torch.from_numpy(a.view(np.float64).copy()).cuda()
@@ -165,6 +187,25 @@ def test_ranges_add_and_host_output():
         P.tn_contract_stem(plan, 0, (1 << nsl) + 1, out)
     with pytest.raises(P.TnError):
         P.tn_contract_stem(plan, 3, 2, out)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3", "bf16x3", "bf16x1"])
+def test_stem_gemm_steps_per_precision(prec):
+    # gemm_min_kn = 2 routes every step with two or more contracted or new
+    # bits through a GEMM (SIMT for fp32, tcgen05 otherwise)
+    c = random_circuit(grid_layout(4, 4), 10, 93)
+    oq = [0, 1, 2, 3, 4, 5]
+    cb = list(random_bits(10, 4))
+    net, plan = _plan(c, oq, cb, cw_limit=9, restarts=3, min_sliced=2, gemm_min_kn=2)
+    assert P.tn_plan_info(plan)["n_gemm_steps"] > 0
+    P.tn_plan_prepare(plan)
+    nsl = P.tn_plan_info(plan)["n_sliced"]
+    got = run(plan, 0, 1 << nsl, prec=prec)[0]
+    ref = oracle.sv_amplitudes(c, oq, cb)
+    # a single BF16 product per step is reported, not gated: ~2^-9 per step
+    # over tens of steps; here it only has to stay a sane approximation
+    tol = {"fp32": TOL, "tf32x3": TOL, "bf16x3": 1e-4, "bf16x1": 0.1}[prec]
+    assert rel_l2(got, ref) < tol, rel_l2(got, ref)
 
 
 def test_all_qubits_open_is_statevector():
