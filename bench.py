@@ -236,6 +236,7 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=60.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--tile-bits", type=int, default=0)
+    ap.add_argument("--max-pass-steps", type=int, default=0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -265,6 +266,8 @@ def main():
     popts = plan_options(name)
     if args.tile_bits:
         popts["tile_bits"] = args.tile_bits
+    if args.max_pass_steps:
+        popts["max_pass_steps"] = args.max_pass_steps
     plan = P.tn_plan_create(net, **popts)
     plan_s = time.perf_counter() - t0
     P.tn_plan_prepare(plan, stream=stream)

@@ -92,6 +92,9 @@ typedef struct {
     int32_t tile_bits;        /* fused-pass tile size log2 (0 = auto, <= 12) */
     int32_t max_pass_steps;   /* steps fused into one pass (0 = auto) */
     int32_t gemm_min_kn;      /* steps with k or n >= this run as GEMM (0 = auto) */
+    int32_t merge_group;      /* Supp. A.3 branch merging: merge runs of this many
+                                 consecutive stem branches into one (0/1 = off) */
+    int32_t merge_rank_cap;   /* largest rank of a merged branch (0 = 10) */
     uint64_t seed;
 } tn_plan_opts;
 
@@ -211,6 +214,59 @@ tn_status tn_contract_stem_noalloc(tn_plan *plan, uint64_t slice_begin, uint64_t
 
 void tn_plan_destroy(tn_plan *plan);
 void tn_network_destroy(tn_network *net);
+
+/* ---- learned step-time cost model and plan search (no counterpart in the
+ * paper, whose order search is KaHyPar + CMA-ES; here candidate plans are
+ * scored per kernel launch) ---- */
+
+/* Features of each kernel launch of one batch, in launch order (the order of
+ * tn_plan_profile's records of kinds 0-2): is_pass, is_gemm, is_permute,
+ * log2(items)/16, r_in/32, r_out/32, steps/8, sum k/16, sum n/16,
+ * tile bits in/16, tile bits out/16, log2(bytes)/40, log2(flops+1)/50,
+ * GEMM precision one-hot (tf32x3, bf16x3, bf16x1). flop_ms receives the plain
+ * FLOP-and-memory model's time of each launch (max of bytes / HBM bandwidth
+ * and flops / arithmetic rate, plus launch overhead). */
+#define TN_N_FEATURES 16
+tn_status tn_plan_features(const tn_plan *plan, tn_precision prec, tn_exec_mode mode, float *X,
+                           double *flop_ms, int32_t max_rows, int32_t *n_rows);
+
+/* MLP n_in -> h1 (ReLU) -> h2 (ReLU) -> 1, trained and run on the GPU by the
+ * library's own kernels. Parameters, one FP32 vector: W1 [h1][n_in], b1 [h1],
+ * W2 [h2][h1], b2 [h2], W3 [h2], b3. Loss: mean squared error. Host arrays:
+ * X row-major [rows][n_in], targets t [rows]. */
+typedef struct tn_mlp tn_mlp;
+tn_status tn_mlp_create(int32_t n_in, int32_t h1, int32_t h2, uint64_t seed, tn_mlp **out);
+tn_status tn_mlp_n_params(const tn_mlp *m, int64_t *n);
+tn_status tn_mlp_set_params(tn_mlp *m, const float *params, int64_t n);
+tn_status tn_mlp_get_params(const tn_mlp *m, float *params, int64_t n);
+/* One forward + backward pass over all rows: loss and gradient (grad may be NULL). */
+tn_status tn_mlp_loss_grad(tn_mlp *m, const float *X, const float *t, int32_t rows,
+                           double *loss, float *grad);
+/* Mini-batch Adam; final_loss = mean batch loss of the last epoch. */
+tn_status tn_mlp_train(tn_mlp *m, const float *X, const float *t, int32_t rows, int32_t epochs,
+                       int32_t batch, float lr, uint64_t seed, double *final_loss);
+tn_status tn_mlp_predict(tn_mlp *m, const float *X, int32_t rows, float *y);
+void tn_mlp_destroy(tn_mlp *m);
+
+typedef struct {
+    int32_t n_seeds;        /* stem-growth seeds (each gives 3 x 5 x 3 variants) */
+    double judge_factor;    /* fall back if the MLP pick's plain-model time exceeds
+                               this factor times the plain model's best (0 = 4) */
+} tn_search_opts;
+
+typedef struct {
+    int32_t n_candidates, n_launch_rows, used_mlp;
+    tn_plan_opts chosen, mlp_pick, flop_pick;
+    double mlp_pick_mlp_ms, mlp_pick_flop_ms;   /* predicted time over all slices */
+    double flop_pick_mlp_ms, flop_pick_flop_ms;
+} tn_search_report;
+
+/* Search candidate plans (base options with varied seed, tile bits, steps per
+ * pass and branch merging), score every launch of every candidate with the
+ * MLP (NULL: plain model only) for precision prec, and return the chosen plan
+ * (not prepared) and a report of both models' picks. */
+tn_status tn_plan_search(tn_network *net, const tn_plan_opts *base, const tn_search_opts *so,
+                         tn_mlp *mlp, tn_precision prec, tn_plan **out, tn_search_report *report);
 
 /* Sec. 2: linear XEB 2^n <p> - 1 of count amplitudes (interleaved re, im,
  * device memory), p = |amp|^2, computed in FP64 on the device. out is a host

@@ -8,7 +8,7 @@ to Python. There is no CPU path: calls fail if the library is missing.
 from .binding import (  # noqa: F401
     Network, Plan, TnError, load, make_opts, tn_build_network, tn_cgemm, tn_contract_stem, tn_contract_stem_noalloc,
     tn_linear_xeb, tn_permute, tn_plan_create, tn_plan_export, tn_plan_info, tn_plan_prepare,
-    tn_plan_steps, tn_plan_profile, tn_version, EXPORTED, PREC, MODE,
+    tn_plan_steps, tn_plan_profile, tn_version, tn_plan_features, tn_plan_search, Mlp, N_FEATURES, EXPORTED, PREC, MODE,
 )
 
 

@@ -29,8 +29,11 @@ EXPORTED = [
     "tn_plan_export", "tn_plan_steps", "tn_contract_stem", "tn_contract_stem_noalloc",
     "tn_plan_profile", "tn_plan_destroy",
     "tn_network_destroy", "tn_linear_xeb", "tn_permute", "tn_cgemm", "tn_last_error",
-    "tn_version",
+    "tn_version", "tn_plan_features", "tn_mlp_create", "tn_mlp_n_params", "tn_mlp_set_params",
+    "tn_mlp_get_params", "tn_mlp_loss_grad", "tn_mlp_train", "tn_mlp_predict", "tn_mlp_destroy",
+    "tn_plan_search",
 ]
+N_FEATURES = 16
 
 
 class TnError(RuntimeError):
@@ -50,7 +53,8 @@ class tn_plan_opts(C.Structure):
                 ("restarts", C.c_int32), ("local_opt_iters", C.c_int32),
                 ("branch_rank", C.c_int32), ("slice_batch", C.c_int32),
                 ("tile_bits", C.c_int32), ("max_pass_steps", C.c_int32),
-                ("gemm_min_kn", C.c_int32), ("seed", C.c_uint64)]
+                ("gemm_min_kn", C.c_int32), ("merge_group", C.c_int32),
+                ("merge_rank_cap", C.c_int32), ("seed", C.c_uint64)]
 
 
 class tn_plan_stats(C.Structure):
@@ -73,6 +77,17 @@ class tn_launch_record(C.Structure):
                 ("r_out", C.c_int32), ("n_steps", C.c_int32), ("k", C.c_int32), ("n", C.c_int32),
                 ("items", C.c_int32), ("ms", C.c_double), ("bytes", C.c_double),
                 ("flops", C.c_double)]
+
+
+class tn_search_opts(C.Structure):
+    _fields_ = [("n_seeds", C.c_int32), ("judge_factor", C.c_double)]
+
+
+class tn_search_report(C.Structure):
+    _fields_ = [("n_candidates", C.c_int32), ("n_launch_rows", C.c_int32), ("used_mlp", C.c_int32),
+                ("chosen", tn_plan_opts), ("mlp_pick", tn_plan_opts), ("flop_pick", tn_plan_opts),
+                ("mlp_pick_mlp_ms", C.c_double), ("mlp_pick_flop_ms", C.c_double),
+                ("flop_pick_mlp_ms", C.c_double), ("flop_pick_flop_ms", C.c_double)]
 
 
 _lib = None
@@ -105,12 +120,25 @@ def load():
     L.tn_linear_xeb.argtypes = [vp, i64, i32, vp, C.POINTER(C.c_double)]
     L.tn_permute.argtypes = [vp, vp, i32, vp, vp]
     L.tn_cgemm.argtypes = [vp, vp, vp, i64, i64, i64, i64, i64, i64, i64, C.c_int, vp]
+    L.tn_plan_features.argtypes = [vp, C.c_int, C.c_int, vp, vp, i32, vp]
+    L.tn_mlp_create.argtypes = [i32, i32, i32, u64, C.POINTER(vp)]
+    L.tn_mlp_n_params.argtypes = [vp, C.POINTER(i64)]
+    L.tn_mlp_set_params.argtypes = [vp, vp, i64]
+    L.tn_mlp_get_params.argtypes = [vp, vp, i64]
+    L.tn_mlp_loss_grad.argtypes = [vp, vp, vp, i32, C.POINTER(C.c_double), vp]
+    L.tn_mlp_train.argtypes = [vp, vp, vp, i32, i32, i32, C.c_float, u64, C.POINTER(C.c_double)]
+    L.tn_mlp_predict.argtypes = [vp, vp, i32, vp]
+    L.tn_mlp_destroy.argtypes = [vp]
+    L.tn_mlp_destroy.restype = None
+    L.tn_plan_search.argtypes = [vp, C.POINTER(tn_plan_opts), C.POINTER(tn_search_opts), vp, C.c_int,
+                                 C.POINTER(vp), C.POINTER(tn_search_report)]
     L.tn_last_error.restype = C.c_char_p
     L.tn_last_error.argtypes = []
     L.tn_version.restype = C.c_char_p
     L.tn_version.argtypes = []
     for name in EXPORTED:
-        if name not in ("tn_plan_destroy", "tn_network_destroy", "tn_last_error", "tn_version"):
+        if name not in ("tn_plan_destroy", "tn_network_destroy", "tn_last_error", "tn_version",
+                        "tn_mlp_destroy"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -190,7 +218,7 @@ def make_opts(**kw) -> tn_plan_opts:
     o = tn_plan_opts()
     defaults = dict(cw_limit=30, min_sliced=0, max_sliced=40, restarts=8, local_opt_iters=4,
                     branch_rank=4, slice_batch=0, tile_bits=0, max_pass_steps=0, gemm_min_kn=0,
-                    seed=0x5EED)
+                    merge_group=0, merge_rank_cap=0, seed=0x5EED)
     defaults.update(kw)
     for k, v in defaults.items():
         setattr(o, k, int(v))
@@ -322,3 +350,92 @@ def tn_cgemm(A, B, Cm, M: int, K: int, N: int, batch: int = 1, strideA: int = 0,
 
 def tn_version() -> str:
     return load().tn_version().decode()
+
+
+# ------------------------------------------------------------ cost models
+
+def tn_plan_features(plan: Plan, prec: str = "fp32", mode: str = "fused"):
+    """Per-launch features [rows, 16] and plain-model times [rows] (ms)."""
+    L = load()
+    n = C.c_int32()
+    _check(L.tn_plan_features(plan.handle, PREC[prec], MODE[mode], None, None, 0, C.byref(n)))
+    X = np.zeros((max(n.value, 1), N_FEATURES), dtype=np.float32)
+    ms = np.zeros(max(n.value, 1), dtype=np.float64)
+    w = C.c_int32()
+    _check(L.tn_plan_features(plan.handle, PREC[prec], MODE[mode], X.ctypes.data, ms.ctypes.data,
+                              n.value, C.byref(w)))
+    return X[:w.value], ms[:w.value]
+
+
+class Mlp:
+    """Handle of the library's GPU MLP cost model."""
+
+    def __init__(self, n_in: int = N_FEATURES, h1: int = 64, h2: int = 64, seed: int = 1):
+        L = load()
+        h = C.c_void_p()
+        _check(L.tn_mlp_create(n_in, h1, h2, seed, C.byref(h)))
+        self.handle = h
+        self.n_in, self.h1, self.h2 = n_in, h1, h2
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.tn_mlp_destroy(self.handle)
+            self.handle = None
+
+    def n_params(self) -> int:
+        n = C.c_int64()
+        _check(load().tn_mlp_n_params(self.handle, C.byref(n)))
+        return n.value
+
+    def get_params(self) -> np.ndarray:
+        p = np.zeros(self.n_params(), dtype=np.float32)
+        _check(load().tn_mlp_get_params(self.handle, p.ctypes.data, p.size))
+        return p
+
+    def set_params(self, p) -> None:
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _check(load().tn_mlp_set_params(self.handle, p.ctypes.data, p.size))
+
+    def loss_grad(self, X, t):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        t = np.ascontiguousarray(t, dtype=np.float32)
+        loss = C.c_double()
+        g = np.zeros(self.n_params(), dtype=np.float32)
+        _check(load().tn_mlp_loss_grad(self.handle, X.ctypes.data, t.ctypes.data, len(t),
+                                       C.byref(loss), g.ctypes.data))
+        return loss.value, g
+
+    def train(self, X, t, epochs=200, batch=256, lr=1e-3, seed=1) -> float:
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        t = np.ascontiguousarray(t, dtype=np.float32)
+        loss = C.c_double()
+        _check(load().tn_mlp_train(self.handle, X.ctypes.data, t.ctypes.data, len(t), epochs, batch,
+                                   lr, seed, C.byref(loss)))
+        return loss.value
+
+    def predict(self, X) -> np.ndarray:
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        y = np.zeros(len(X), dtype=np.float32)
+        _check(load().tn_mlp_predict(self.handle, X.ctypes.data, len(X), y.ctypes.data))
+        return y
+
+
+def tn_plan_search(net: Network, mlp: Optional[Mlp] = None, prec: str = "fp32", n_seeds: int = 3,
+                   judge_factor: float = 4.0, **opts):
+    """Search candidate plans; returns (plan, report dict)."""
+    L = load()
+    o = make_opts(**opts)
+    so = tn_search_opts(n_seeds, judge_factor)
+    rep = tn_search_report()
+    h = C.c_void_p()
+    _check(L.tn_plan_search(net.handle, C.byref(o), C.byref(so), mlp.handle if mlp else None,
+                            PREC[prec], C.byref(h), C.byref(rep)))
+
+    def od(x):
+        return {f: getattr(x, f) for f, _ in tn_plan_opts._fields_}
+    report = {"n_candidates": rep.n_candidates, "n_launch_rows": rep.n_launch_rows,
+              "used_mlp": bool(rep.used_mlp), "chosen": od(rep.chosen), "mlp_pick": od(rep.mlp_pick),
+              "flop_pick": od(rep.flop_pick), "mlp_pick_mlp_ms": rep.mlp_pick_mlp_ms,
+              "mlp_pick_flop_ms": rep.mlp_pick_flop_ms, "flop_pick_mlp_ms": rep.flop_pick_mlp_ms,
+              "flop_pick_flop_ms": rep.flop_pick_flop_ms}
+    return Plan(h, net), report

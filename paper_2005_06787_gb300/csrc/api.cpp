@@ -16,6 +16,10 @@ struct tn_network {
 struct tn_plan {
     std::unique_ptr<tn::Plan> p;
 };
+struct tn_mlp {
+    tn::Mlp *m = nullptr;
+    ~tn_mlp() { tn::mlp_destroy(m); }
+};
 
 namespace tn {
 static thread_local std::string g_last_error;
@@ -113,6 +117,7 @@ tn_status tn_plan_create(tn_network *net, const int32_t *order, int32_t n_pairs,
             }
             p->scheme = tn::plan_scheme(p->net, o);
         }
+        if (o.merge_group >= 2) tn::merge_branches(p->net, p->scheme, o.merge_group, o.merge_rank_cap);
         if (p->scheme.cw > 31) tn::fail(TN_ERR_PLAN_INFEASIBLE, "contraction width above 31");
         tn::BuiltStem bs = tn::build_stem_plan(p->net, p->scheme, o);
         p->sp = std::move(bs.sp);
@@ -225,6 +230,113 @@ tn_status tn_contract_stem_noalloc(tn_plan *plan, uint64_t slice_begin, uint64_t
         if (!plan) tn::fail(TN_ERR_INVALID_ARG, "null plan");
         tn::plan_contract_noalloc(*plan->p, slice_begin, slice_end, (cudaStream_t)cuda_stream,
                                   amps_out, accumulate);
+    });
+}
+
+tn_status tn_plan_features(const tn_plan *plan, tn_precision prec, tn_exec_mode mode, float *X,
+                           double *flop_ms, int32_t max_rows, int32_t *n_rows) {
+    return guard([&] {
+        if (!plan || !n_rows) tn::fail(TN_ERR_INVALID_ARG, "null argument");
+        const tn::Plan &p = *plan->p;
+        const int nsl = (int)p.scheme.sliced_list.size();
+        const int npre = std::max(p.n_prefix, 1);
+        const int items = mode == TN_EXEC_FUSED
+                              ? (p.prepared ? p.SB : tn::choose_batch(p.sp.max_rank, nsl, npre, p.opts.slice_batch)) * npre
+                              : 1;
+        auto L = tn::launch_list(p.sp, mode, items);
+        int w = 0;
+        for (size_t i = 0; i < L.size() && w < max_rows; ++i, ++w) {
+            if (X) tn::launch_features(L[i], prec, X + (size_t)w * tn::N_FEATURES);
+            if (flop_ms) flop_ms[w] = tn::flop_model_ms(L[i], prec);
+        }
+        *n_rows = max_rows > 0 ? w : (int32_t)L.size();
+    });
+}
+
+tn_status tn_mlp_create(int32_t n_in, int32_t h1, int32_t h2, uint64_t seed, tn_mlp **out) {
+    return guard([&] {
+        if (!out) tn::fail(TN_ERR_INVALID_ARG, "null argument");
+        auto *h = new tn_mlp;
+        try {
+            h->m = tn::mlp_create(n_in, h1, h2, seed);
+        } catch (...) {
+            delete h;
+            throw;
+        }
+        *out = h;
+    });
+}
+tn_status tn_mlp_n_params(const tn_mlp *m, int64_t *n) {
+    return guard([&] {
+        if (!m || !n) tn::fail(TN_ERR_INVALID_ARG, "null argument");
+        *n = tn::mlp_n_params(*m->m);
+    });
+}
+tn_status tn_mlp_set_params(tn_mlp *m, const float *params, int64_t n) {
+    return guard([&] {
+        if (!m || !params) tn::fail(TN_ERR_INVALID_ARG, "null argument");
+        tn::mlp_set_params(*m->m, params, n);
+    });
+}
+tn_status tn_mlp_get_params(const tn_mlp *m, float *params, int64_t n) {
+    return guard([&] {
+        if (!m || !params) tn::fail(TN_ERR_INVALID_ARG, "null argument");
+        tn::mlp_get_params(*m->m, params, n);
+    });
+}
+tn_status tn_mlp_loss_grad(tn_mlp *m, const float *X, const float *t, int32_t rows, double *loss,
+                           float *grad) {
+    return guard([&] {
+        if (!m || !X || !t || !loss) tn::fail(TN_ERR_INVALID_ARG, "null argument");
+        tn::mlp_loss_grad_host(*m->m, X, t, rows, loss, grad);
+    });
+}
+tn_status tn_mlp_train(tn_mlp *m, const float *X, const float *t, int32_t rows, int32_t epochs,
+                       int32_t batch, float lr, uint64_t seed, double *final_loss) {
+    return guard([&] {
+        if (!m || !X || !t) tn::fail(TN_ERR_INVALID_ARG, "null argument");
+        const double l = tn::mlp_train(*m->m, X, t, rows, epochs, batch, lr, seed);
+        if (final_loss) *final_loss = l;
+    });
+}
+tn_status tn_mlp_predict(tn_mlp *m, const float *X, int32_t rows, float *y) {
+    return guard([&] {
+        if (!m || !X || !y || rows < 0) tn::fail(TN_ERR_INVALID_ARG, "bad argument");
+        tn::mlp_predict(*m->m, X, rows, y);
+    });
+}
+void tn_mlp_destroy(tn_mlp *m) { delete m; }
+
+tn_status tn_plan_search(tn_network *net, const tn_plan_opts *base, const tn_search_opts *so,
+                         tn_mlp *mlp, tn_precision prec, tn_plan **out, tn_search_report *report) {
+    return guard([&] {
+        if (!net || !out) tn::fail(TN_ERR_INVALID_ARG, "null argument");
+        tn_plan_opts o = base ? *base : default_opts();
+        if (o.cw_limit <= 0) o.cw_limit = 30;
+        tn_search_opts s{};
+        if (so) s = *so;
+        tn::SearchResult r = tn::plan_search(net->net, o, s, mlp ? mlp->m : nullptr, prec);
+        auto p = std::make_unique<tn::Plan>();
+        p->net = net->net;
+        p->opts = r.opts;
+        p->scheme = std::move(r.scheme);
+        p->sp = std::move(r.stem.sp);
+        p->layouts = std::move(r.stem.layouts);
+        if (report) {
+            report->n_candidates = r.n_candidates;
+            report->n_launch_rows = r.n_launch_rows;
+            report->used_mlp = r.used_mlp ? 1 : 0;
+            report->chosen = r.opts;
+            report->mlp_pick = r.mlp_opts;
+            report->flop_pick = r.flop_opts;
+            report->mlp_pick_mlp_ms = r.mlp_pick_mlp_ms;
+            report->mlp_pick_flop_ms = r.mlp_pick_flop_ms;
+            report->flop_pick_mlp_ms = r.flop_pick_mlp_ms;
+            report->flop_pick_flop_ms = r.flop_pick_flop_ms;
+        }
+        auto *h = new tn_plan;
+        h->p = std::move(p);
+        *out = h;
     });
 }
 

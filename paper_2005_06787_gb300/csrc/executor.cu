@@ -56,23 +56,27 @@ static SmallContract make_contract(const std::vector<int> &la, const std::vector
             if (l[i] == e) return (int)i;
         return -1;
     };
+    // an output edge comes from A, from B, or from both (a batch edge: a
+    // sliced edge shared by the two, indexed in both and not summed)
+    int batch = 0;
     for (int j = 0; j < d.rc; ++j) {
         d.a_out[j] = pos(la, lc[(size_t)j]);
         d.b_out[j] = pos(lb, lc[(size_t)j]);
-        if ((d.a_out[j] >= 0) == (d.b_out[j] >= 0))
-            fail(TN_ERR_INVALID_ARG, "internal: output edge must come from exactly one input");
+        if (d.a_out[j] < 0 && d.b_out[j] < 0)
+            fail(TN_ERR_INVALID_ARG, "internal: output edge in neither input");
+        if (d.a_out[j] >= 0 && d.b_out[j] >= 0) ++batch;
     }
     d.k = 0;
     for (int i = 0; i < d.ra; ++i) {
         int pb = pos(lb, la[(size_t)i]);
-        if (pb >= 0) {
-            if (pos(lc, la[(size_t)i]) >= 0) fail(TN_ERR_INVALID_ARG, "internal: shared edge kept");
+        if (pb >= 0 && pos(lc, la[(size_t)i]) < 0) {
             d.a_k[d.k] = i;
             d.b_k[d.k] = pb;
             d.k++;
         }
     }
-    if (d.ra + d.rb - 2 * d.k != d.rc) fail(TN_ERR_INVALID_ARG, "internal: edge count mismatch");
+    if (d.ra + d.rb - 2 * d.k - batch != d.rc)
+        fail(TN_ERR_INVALID_ARG, "internal: edge count mismatch");
     return d;
 }
 
@@ -148,6 +152,9 @@ void plan_prepare(Plan &p, const uint8_t *prefixes, int n_prefixes, cudaStream_t
         pool += ((sz * copies) + 63) & ~63ll;
     }
     p.pool_elems = pool;
+    if (pool > ((int64_t)1 << 33))
+        fail(TN_ERR_UNSUPPORTED, "pre-computed branches would exceed 64 GiB (a branch keeps too many "
+                                 "sliced edges as dimensions)");
     // every branch read stays inside the pool: last prefix copy, all sliced
     // bits set, a full 2^(k+n) matrix (or the whole seed tensor)
     for (int c = 0; c < C; ++c) {
@@ -167,6 +174,7 @@ void plan_prepare(Plan &p, const uint8_t *prefixes, int n_prefixes, cudaStream_t
     // ---- pre-compute each cluster (per prefix when it holds a projector)
     // scratch: the largest sum of intermediate sizes of one cluster
     auto leaf_layout = [&](int leaf) { return net.leaves[(size_t)leaf].edges; };
+    const Bits &sliced = p.scheme.sliced;
     int64_t scratch_need = 0;
     std::vector<std::vector<std::vector<int>>> node_layouts((size_t)C);
     for (int c = 0; c < C; ++c) {
@@ -182,8 +190,10 @@ void plan_prepare(Plan &p, const uint8_t *prefixes, int n_prefixes, cudaStream_t
             if (k + 1 == cl.pairs.size()) {
                 lc = p.layouts[(size_t)c].bits;
             } else {
+                // shared edges are summed, except sliced ones (kept as batch dims)
                 for (int e : la)
-                    if (std::find(lb.begin(), lb.end(), e) == lb.end()) lc.push_back(e);
+                    if (std::find(lb.begin(), lb.end(), e) == lb.end() || sliced.test(e))
+                        lc.push_back(e);
                 for (int e : lb)
                     if (std::find(la.begin(), la.end(), e) == la.end()) lc.push_back(e);
             }
@@ -256,14 +266,7 @@ void plan_prepare(Plan &p, const uint8_t *prefixes, int n_prefixes, cudaStream_t
     // ---- stem buffers: fused batches hold n_prefix * SB items
     const int maxr = p.sp.max_rank;
     const int nsl = (int)p.scheme.sliced_list.size();
-    int64_t SB = p.opts.slice_batch > 0 ? p.opts.slice_batch : 0;
-    if (SB == 0) {
-        const int64_t budget = (int64_t)1 << 27;  // entries per buffer (1 GiB)
-        SB = std::max<int64_t>(1, budget / (((int64_t)1 << maxr) * n_prefixes));
-    }
-    SB = std::min<int64_t>(SB, nsl >= 62 ? SB : ((int64_t)1 << nsl));
-    SB = std::min<int64_t>(SB, 65535 / n_prefixes);
-    SB = std::max<int64_t>(SB, 1);
+    const int64_t SB = choose_batch(maxr, nsl, n_prefixes, p.opts.slice_batch);
     p.SB = (int)SB;
     const int64_t items = SB * n_prefixes;
     p.buf_elems = std::max<int64_t>(items << maxr, (int64_t)1 << maxr);

@@ -167,6 +167,7 @@ Scheme plan_scheme(const Network &net, const tn_plan_opts &opts);
 Scheme scheme_from_order(const Network &net, const std::vector<std::pair<int, int>> &order,
                          const std::vector<int> &sliced, const tn_plan_opts &opts);
 void evaluate_scheme(const Network &net, Scheme &s);
+void merge_branches(const Network &net, Scheme &s, int group, int rank_cap);
 std::vector<std::pair<int, int>> export_order(const Network &net, const Scheme &s);
 
 // ----------------------------------------------------------------- device plan

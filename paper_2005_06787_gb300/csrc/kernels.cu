@@ -276,10 +276,8 @@ __global__ void small_contract_kernel(const double2 *__restrict__ A, const doubl
         int64_t ia = 0, ib = 0;
         for (int j = 0; j < d.rc; ++j) {
             if (!((o >> j) & 1)) continue;
-            if (d.a_out[j] >= 0)
-                ia += (int64_t)1 << d.a_out[j];
-            else
-                ib += (int64_t)1 << d.b_out[j];
+            if (d.a_out[j] >= 0) ia += (int64_t)1 << d.a_out[j];
+            if (d.b_out[j] >= 0) ib += (int64_t)1 << d.b_out[j];
         }
         double re, im;
         if (!B) {

@@ -11,8 +11,39 @@
 
 namespace tn {
 
-struct BuiltStem;
 BuiltStem build_stem_plan(const Network &net, const Scheme &s, const tn_plan_opts &o);
+
+// ---- cost models and search (costmodel.cpp, mlp.cu)
+constexpr int N_FEATURES = TN_N_FEATURES;
+struct LaunchDesc {
+    int kind;  // 0 fused pass, 1 GEMM step, 2 permute (plain)
+    int items, r_in, r_out, n_steps, sum_k, sum_n, t_in, t_out;
+    double bytes, flops;
+};
+int choose_batch(int max_rank, int n_sliced, int n_prefixes, int slice_batch);
+std::vector<LaunchDesc> launch_list(const StemPlan &sp, tn_exec_mode mode, int items);
+void launch_features(const LaunchDesc &d, tn_precision prec, float *f);
+double flop_model_ms(const LaunchDesc &d, tn_precision prec);
+struct Mlp;
+Mlp *mlp_create(int n_in, int h1, int h2, uint64_t seed);
+void mlp_destroy(Mlp *m);
+int64_t mlp_n_params(const Mlp &m);
+void mlp_set_params(Mlp &m, const float *p, int64_t n);
+void mlp_get_params(const Mlp &m, float *p, int64_t n);
+void mlp_loss_grad_host(Mlp &m, const float *X, const float *t, int rows, double *loss, float *grad);
+double mlp_train(Mlp &m, const float *X, const float *t, int rows, int epochs, int batch, float lr,
+                 uint64_t seed);
+void mlp_predict(Mlp &m, const float *X, int rows, float *y);
+struct SearchResult {
+    int n_candidates = 0, n_launch_rows = 0;
+    bool used_mlp = false;
+    tn_plan_opts opts{}, mlp_opts{}, flop_opts{};
+    double mlp_pick_mlp_ms = 0, mlp_pick_flop_ms = 0, flop_pick_mlp_ms = 0, flop_pick_flop_ms = 0;
+    Scheme scheme;
+    BuiltStem stem;
+};
+SearchResult plan_search(const Network &net, const tn_plan_opts &base, const tn_search_opts &so,
+                         Mlp *mlp, tn_precision prec);
 
 struct DeviceArena {
     void *ptr = nullptr;

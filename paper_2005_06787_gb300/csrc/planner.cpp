@@ -465,11 +465,22 @@ Scheme scheme_from_order(const Network &net, const std::vector<std::pair<int, in
         return c;
     };
     double total = sub[(size_t)root];
+    // storage bits of a subtree kept as a pre-computed branch: its output
+    // edges plus every sliced edge touching its leaves (kept as dimensions)
+    std::vector<Bits> touch((size_t)N);
+    for (int i = 0; i < L; ++i) touch[(size_t)i] = out[(size_t)i] & s.sliced;
+    for (int k = 0; k < L - 1; ++k) {
+        const int id = L + k;
+        touch[(size_t)id] = touch[(size_t)lc[(size_t)id]] | touch[(size_t)rc[(size_t)id]];
+    }
+    auto storage_bits = [&](int v) { return count_or(out[(size_t)v], touch[(size_t)v]); };
     std::vector<int> path;  // stem nodes root -> bottom
     int u = root;
     while (u >= L) {
         double cl = sub[(size_t)lc[(size_t)u]], cr = sub[(size_t)rc[(size_t)u]];
-        if (sub[(size_t)u] < total + std::log2(0.01) && !path.empty()) break;
+        // the stem ends where the rest is cheap (< 1% of the cost) and small
+        // enough to store as one branch
+        if (sub[(size_t)u] < total + std::log2(0.01) && !path.empty() && storage_bits(u) <= 20) break;
         path.push_back(u);
         u = (cl >= cr) ? lc[(size_t)u] : rc[(size_t)u];
     }
@@ -497,6 +508,51 @@ Scheme scheme_from_order(const Network &net, const std::vector<std::pair<int, in
     evaluate_scheme(net, s);
     (void)o;
     return s;
+}
+
+// Supp. A.3 "Branch merging": merge each run of `group` consecutive stem
+// branches into one branch (the pair list of the first, then of the next,
+// then one pair joining them), so the stem absorbs one larger tensor at once.
+// Runs stop early when the merged rank (unsliced) would exceed rank_cap or
+// two members share a sliced edge (that edge would be summed inside the
+// branch instead of being fixed per slice).
+void merge_branches(const Network &net, Scheme &s, int group, int rank_cap) {
+    if (group < 2 || s.stem_order.empty()) return;
+    if (rank_cap <= 0) rank_cap = 10;
+    std::vector<Cluster> out;
+    out.push_back(s.clusters[(size_t)s.seed_cluster]);
+    std::vector<int> order;
+    size_t i = 0;
+    while (i < s.stem_order.size()) {
+        Cluster m = s.clusters[(size_t)s.stem_order[i]];
+        int members = 1;
+        size_t j = i + 1;
+        while (j < s.stem_order.size() && members < group) {
+            const Cluster &b = s.clusters[(size_t)s.stem_order[j]];
+            if ((m.out & b.out & s.sliced).any()) break;
+            if ((m.out ^ b.out).andnot(s.sliced).count() > rank_cap) break;
+            // root refs of m and b within the merged pair list
+            const int base = (int)m.pairs.size();
+            const int ra = m.pairs.empty() ? m.leaves[0] : -(int)m.pairs.size();
+            int rb = b.pairs.empty() ? b.leaves[0] : -((int)b.pairs.size() + base);
+            for (auto p : b.pairs) {
+                auto fix = [&](int r) { return r >= 0 ? r : -((-r - 1) + base + 1); };
+                m.pairs.push_back({fix(p.first), fix(p.second)});
+            }
+            m.pairs.push_back({ra, rb});
+            m.leaves.insert(m.leaves.end(), b.leaves.begin(), b.leaves.end());
+            m.out ^= b.out;
+            ++members;
+            ++j;
+        }
+        out.push_back(std::move(m));
+        order.push_back((int)out.size() - 1);
+        i = j;
+    }
+    s.clusters = std::move(out);
+    s.seed_cluster = 0;
+    s.stem_order = std::move(order);
+    evaluate_scheme(net, s);
 }
 
 // SSA order over the leaves: every cluster's internal pairs, then the stem.

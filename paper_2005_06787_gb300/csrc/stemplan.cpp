@@ -299,7 +299,7 @@ BuiltStem build_stem_plan(const Network &net, const Scheme &s, const tn_plan_opt
     BuiltStem R;
     const int T_MAX = (o.tile_bits > 0) ? std::min(o.tile_bits, MAX_TILE_BITS) : 12;
     const int C_BITS = 4;
-    const int max_steps = (o.max_pass_steps > 0) ? std::min(o.max_pass_steps, MAX_PASS_STEPS) : 6;
+    const int max_steps = (o.max_pass_steps > 0) ? std::min(o.max_pass_steps, MAX_PASS_STEPS) : 8;
     const int gemm_min = (o.gemm_min_kn > 0) ? o.gemm_min_kn : 5;
     const Bits &sl = s.sliced;
     std::vector<Bits> B;
@@ -351,10 +351,13 @@ BuiltStem build_stem_plan(const Network &net, const Scheme &s, const tn_plan_opt
     }
     for (size_t c = 0; c < s.clusters.size(); ++c) {
         BranchLayout &bl = R.layouts[c];
-        for (int e : (s.clusters[c].out & sl).list()) {
-            // slice-bit order = position in sliced_list
-            bl.sliced_edges.push_back(e);
-        }
+        // every sliced edge touching the cluster, including edges between two
+        // of its own leaves: those are carried through the branch contraction
+        // as batch dimensions (never summed) and fixed by the slice offset
+        Bits touch(net.n_edges());
+        for (int leaf : s.clusters[c].leaves)
+            for (int e : net.leaves[(size_t)leaf].edges) touch.set(e);
+        for (int e : (touch & sl).list()) bl.sliced_edges.push_back(e);
         std::sort(bl.sliced_edges.begin(), bl.sliced_edges.end(), [&](int a, int b) {
             return std::find(s.sliced_list.begin(), s.sliced_list.end(), a) <
                    std::find(s.sliced_list.begin(), s.sliced_list.end(), b);
