@@ -224,6 +224,81 @@ def _host_plan(name):
     return order, wires, P.tn_plan_info(plan)
 
 
+def run_learned(args):
+    """20-cycle workload: plan search scored by the learned MLP (trained on
+    launch timings of the 30-qubit and 53-qubit 12/14-cycle workloads) versus
+    the plain FLOP-and-memory model; 64 seeded slices of each pick timed and
+    extrapolated to the full slice count; predicted vs measured per slice."""
+    import torch
+    import paper_2005_06787_gb300 as P
+    from paper_2005_06787_gb300 import learned
+    from synthetic.circuits import SplitMix64
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    t_start = time.perf_counter()
+    rows = []
+    for wl in ("grid5x6_m14", "diag53_m12", "diag53_m14"):
+        c, oq, cb = workload_inputs(wl)
+        net = P.tn_build_network(c, oq, cb)
+        for plan in learned.plan_variants(net, plan_options(wl), tiles=(11, 12), steps=(4, 8),
+                                          merges=(0, 3)):
+            P.tn_plan_prepare(plan, stream=stream)
+            precs = ("fp32", "tf32x3") if P.tn_plan_info(plan)["n_gemm_steps"] else ("fp32",)
+            for prec in precs:
+                rows.append(learned.profile_rows(plan, prec, "fused", repeats=2))
+            del plan
+            torch.cuda.empty_cache()
+    X = np.concatenate([r[0] for r in rows])
+    y = np.concatenate([r[1] for r in rows])
+    mlp = learned.train_cost_model(X, y, epochs=600)
+    fit = float(np.corrcoef(mlp.predict(X), y)[0, 1])
+    train_s = time.perf_counter() - t_start
+    name = "diag53_m20"
+    c, oq, cb = workload_inputs(name)
+    net = P.tn_build_network(c, oq, cb)
+    base = dict(plan_options(name), max_sliced=60, restarts=4)
+    out = torch.zeros(2 * (1 << len(oq)), dtype=torch.float64, device="cuda")
+    res = {}
+    for label, m in (("mlp", mlp), ("flop", None)):
+        t0 = time.perf_counter()
+        plan, rep = P.tn_plan_search(net, mlp=m, n_seeds=2, **base)
+        search_s = time.perf_counter() - t0
+        P.tn_plan_prepare(plan, stream=stream)
+        info = P.tn_plan_info(plan)
+        nsl = info["n_sliced"]
+        rng = SplitMix64(CONFIGS[name]["bit_seed"])
+        ids = [rng.next() % (1 << nsl) for _ in range(64)]
+        P.tn_contract_stem(plan, ids[0], ids[0] + 1, out, stream=stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for sid in ids:
+            P.tn_contract_stem(plan, sid, sid + 1, out, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_slice = e0.elapsed_time(e1) / len(ids)
+        Xp, flop_ms = P.tn_plan_features(plan)
+        pred_mlp = float(np.exp(mlp.predict(Xp).astype(np.float64)).sum())
+        res[label] = {"pick": {k: rep["chosen"][k] for k in ("seed", "tile_bits", "max_pass_steps", "merge_group")},
+                      "used_mlp": rep["used_mlp"], "candidates": rep["n_candidates"],
+                      "launch_rows_scored": rep["n_launch_rows"], "search_s": search_s,
+                      "n_sliced": nsl, "cw": info["cw"], "log2_tc": info["log2_tc"],
+                      "measured_ms_per_slice": ms_slice, "predicted_ms_per_slice_mlp": pred_mlp,
+                      "predicted_ms_per_slice_flop": float(flop_ms.sum()),
+                      "extrapolated_days_all_slices": ms_slice * 2.0 ** nsl / 1e3 / 86400,
+                      "stem_tflops": 8 * info["stem_tc_per_slice"] / (ms_slice / 1e3) / 1e12}
+        del plan
+        torch.cuda.empty_cache()
+    line = {"metric": "20-cycle plan chosen by learned vs plain cost model: extrapolated time "
+                      "(64 seeded slices timed)", "value": res["mlp"]["extrapolated_days_all_slices"],
+            "unit": "days", "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": name, "train_rows": int(len(y)), "train_fit_corr": fit,
+                       "train_seconds": train_s},
+            "mlp": res["mlp"], "flop": res["flop"],
+            "gain_vs_flop_model": res["flop"]["extrapolated_days_all_slices"] / res["mlp"]["extrapolated_days_all_slices"]}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -236,6 +311,9 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=60.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--tile-bits", type=int, default=0)
+    ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--learned", action="store_true",
+                    help="20-cycle learned-cost-model plan search instead of the default bench")
     ap.add_argument("--max-pass-steps", type=int, default=0)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -245,6 +323,9 @@ def main():
     build_lib()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.learned:
+        run_learned(args)
         return
 
     import torch
@@ -279,9 +360,10 @@ def main():
     out = torch.zeros(2 * nb, dtype=torch.float64, device="cuda")
     flops_per_slice = 8.0 * info["stem_tc_per_slice"]
 
-    # this rank's slice range: disjoint per rank (weak scaling)
+    # this rank's slice range: disjoint blocks per rank (weak scaling)
+    from paper_2005_06787_gb300.shard import all_reduce_amplitudes, slice_range
     per_rank = (args.warmup + args.steps) * SB
-    base = (rank * per_rank) % max(1, n_slices_total - per_rank + 1)
+    base, _ = slice_range(rank, world, min(per_rank * world, n_slices_total))
 
     def step(i, mode="fused", sb=SB, host_out=None):
         s0 = base + i * sb
@@ -307,6 +389,8 @@ def main():
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
     clocks = clk.summary()
+    if world > 1:  # the one exchange: sum of the partial amplitudes (outside the timed region)
+        all_reduce_amplitudes(out)
     slices_done = args.steps * SB * world
     slices_per_s = slices_done / (ms / 1e3)
     tflops = slices_per_s * flops_per_slice / 1e12
@@ -367,9 +451,48 @@ def main():
                 "peak_source": peak_kind, "share_of_step": d["ms"] / tot_ms if tot_ms else None,
                 "simt_tflops": d["flops"] / (d["ms"] / 1e3) / 1e12}
 
+    order_export, sl_export = P.tn_plan_export(plan)
+    # precision sweep on a branch-merged plan (Supp. A.3): most steps become
+    # GEMM steps, run by the FP32 SIMT GEMM or the tcgen05 GEMM per precision
+    sweep = None
+    if rank == 0 and not args.no_sweep:
+        del plan
+        torch.cuda.empty_cache()
+        mplan = P.tn_plan_create(net, **dict(popts, merge_group=3))
+        P.tn_plan_prepare(mplan, stream=stream)
+        minfo = P.tn_plan_info(mplan)
+        mflops = 8.0 * minfo["stem_tc_per_slice"]
+        peaks_all, _ = measured_peaks()
+        sweep = {"plan": {"merge_group": 3, "stem_steps": minfo["n_stem_steps"],
+                          "gemm_steps": minfo["n_gemm_steps"], "stem_tc_per_slice": minfo["stem_tc_per_slice"]}}
+        for prec in ("fp32", "tf32x3", "bf16x3", "bf16x1"):
+            P.tn_contract_stem(mplan, 0, 1, out, prec=prec, stream=stream)
+            torch.cuda.synchronize()
+            q0 = torch.cuda.Event(enable_timing=True)
+            q1 = torch.cuda.Event(enable_timing=True)
+            q0.record(stream)
+            for i in range(2):
+                P.tn_contract_stem(mplan, 1 + i, 2 + i, out, prec=prec, stream=stream)
+            q1.record(stream)
+            torch.cuda.synchronize()
+            sps = 2 / (q0.elapsed_time(q1) / 1e3)
+            recs = P.tn_plan_profile(mplan, 0, prec=prec, mode="fused", stream=stream)
+            g = [r for r in recs if r["kind"] == 1]
+            gms = sum(r["ms"] for r in g)
+            gtf = sum(r["flops"] for r in g) / (gms / 1e3) / 1e12 if gms else None
+            # executed tensor flops: 3 products for x3, 1 for x1 (algorithmic = one product)
+            mult = {"fp32": 1, "tf32x3": 3, "bf16x3": 3, "bf16x1": 1}[prec]
+            peak = peaks_all.get("bf16_tflops", 1900.0) * (0.5 if prec == "tf32x3" else 1.0)
+            sweep[prec] = {"slices_per_s": sps, "stem_tflops": sps * mflops / 1e12,
+                           "gemm_share": gms / sum(r["ms"] for r in recs),
+                           "gemm_alg_tflops": gtf,
+                           "gemm_exec_frac_of_tensor_peak": (gtf * mult / peak) if (gtf and prec != "fp32") else None}
+        del mplan
+        torch.cuda.empty_cache()
+
     cpu = None
     if rank == 0 and not args.no_cpu:
-        order, sl = P.tn_plan_export(plan)
+        order, sl = order_export, sl_export
         _, _, q, s = net.info()
         wires = [(int(q[e]), int(s[e])) for e in sl]
         tc, secs, done = oracle_sample(name, args.cpu_budget, order, wires, info)
@@ -403,6 +526,7 @@ def main():
             "launch_breakdown": by_kind,
             "plain_breakdown": plain_kind,
             "cpu_baseline": cpu,
+            "precision_sweep": sweep,
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks,
             "amp_norm_check": float(np.linalg.norm(amps)),
