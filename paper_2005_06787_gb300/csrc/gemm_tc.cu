@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "kernels.h"
@@ -296,6 +297,255 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_cgemm_kernel(TcArgs g) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(ncols));
 }
 
+// Persistent variant for the stem's tall-skinny shapes (2K <= 64 real
+// columns of A, 2N <= 256): each block builds the split B once per batch item,
+// keeps two A stages and two TMEM accumulators, and walks 128-row tiles
+// t = blockIdx.x, blockIdx.x + gridDim.x, ... over (item, row tile). While the
+// tensor core multiplies tile i, the threads load and split tile i+1 into the
+// other stage; the epilogue of tile i overlaps the MMAs of tile i+1.
+constexpr int P_K2MAX = 64;
+// dynamic shared memory allowed per block (opt-in limit minus the static
+// barriers), set by tc_gemm_init from the device attribute
+size_t P_SMEM_MAX = 200 * 1024;
+
+template <int PREC>
+__global__ void __launch_bounds__(TC_THREADS, 1) tc_cgemm_persistent(TcArgs g, int64_t n_items) {
+    constexpr int KIND = (PREC == 1) ? 0 : 1;
+    constexpr int ESZ = (KIND == 0) ? 4 : 2;
+    constexpr int KC = 128 / ESZ;        // elements per 128-byte row block
+    constexpr int KSTEP = 32 / ESZ;
+    constexpr bool X3 = PREC != 3;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *sm = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    const int K2 = 2 * g.K, N2 = 2 * g.N;
+    const int nbp = (N2 + 15) & ~15;
+    const int kblocks = (K2 + KC - 1) / KC;               // 128-byte row blocks along K
+    const size_t a_part = (size_t)kblocks * TC_BM * 128;  // one split part of one stage
+    const size_t b_part = (size_t)kblocks * nbp * 128;
+    unsigned char *sA[2][2], *sB[2];
+    {
+        unsigned char *q = sm;
+        for (int st = 0; st < 2; ++st)
+            for (int h = 0; h < 2; ++h) {
+                sA[st][h] = q;
+                if (h == 0 || X3) q += a_part;
+            }
+        sB[0] = q;
+        q += b_part;
+        sB[1] = q;
+    }
+    __shared__ uint64_t bars[2];
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int64_t mtiles = (g.M + TC_BM - 1) / TC_BM;
+    const int64_t n_tiles = mtiles * n_items;
+    uint32_t ncols = 32;
+    while ((int)ncols < 2 * nbp) ncols <<= 1;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                         smem_u32(&tmem_base)), "r"(ncols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&bars[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&bars[1])));
+        asm volatile("fence.mbarrier_init.release.cluster;\n");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    const uint32_t tmem = tmem_base;
+    const uint32_t idesc = make_idesc(KIND == 0 ? 2 : 1, nbp, TC_BM);
+    uint32_t phase[2] = {0u, 0u};
+    bool ok = true;
+
+    // item -> B source (stem steps: branch of (prefix, slice); else strided)
+    auto b_src = [&](int64_t item, bool &valid) -> const float * {
+        valid = true;
+        if (g.use_batch) {
+            const int pl = (int)(item / g.ba.SB);
+            const int64_t s = g.ba.state->slice_base + (item - (int64_t)pl * g.ba.SB);
+            if (s >= g.ba.state->slice_end) {
+                valid = false;
+                return nullptr;
+            }
+            int64_t o = g.br->base + (int64_t)(g.ba.p0 + pl) * g.br->prefix_stride;
+            for (int i = 0; i < g.br->n_sl; ++i)
+                if ((s >> g.br->sl_bit[i]) & 1) o += (int64_t)1 << g.br->sl_pos[i];
+            return reinterpret_cast<const float *>(g.pool + o);
+        }
+        return g.B + item * 2 * g.sB;
+    };
+    auto build_b = [&](const float *B) {
+        for (int i = tid; i < nbp * kblocks * KC; i += TC_THREADS) {
+            const int j = i / (kblocks * KC), kk = i % (kblocks * KC);
+            float v = 0.f;
+            if (j < N2 && kk < K2) {
+                const int nu = j >> 1, d = j & 1, kap = kk >> 1, c = kk & 1;
+                const float re = B[2 * ((int64_t)kap * g.N + nu)];
+                const float im = B[2 * ((int64_t)kap * g.N + nu) + 1];
+                v = (c == d) ? re : (c == 1 ? -im : im);
+            }
+            const uint32_t off = (uint32_t)((kk / KC) * nbp * 128) + sw128(j, (kk % KC) * ESZ);
+            if constexpr (KIND == 0) {
+                float hi, lo;
+                split_tf32(v, hi, lo);
+                *reinterpret_cast<float *>(sB[0] + off) = hi;
+                *reinterpret_cast<float *>(sB[1] + off) = lo;
+            } else {
+                __nv_bfloat16 hi, lo;
+                split_bf16(v, hi, lo);
+                *reinterpret_cast<__nv_bfloat16 *>(sB[0] + off) = hi;
+                if constexpr (X3) *reinterpret_cast<__nv_bfloat16 *>(sB[1] + off) = lo;
+            }
+        }
+    };
+    // load + split the 128 x K2 A tile of tile index t into stage st
+    auto load_a = [&](int64_t t, int st) {
+        const int64_t item = t / mtiles, m0 = (t % mtiles) * TC_BM;
+        const float *A = g.A + item * g.sA;
+        for (int i = tid; i < TC_BM * (K2 / 4); i += TC_THREADS) {
+            const int r = i / (K2 / 4), k4 = (i % (K2 / 4)) * 4;
+            const int64_t m = m0 + r;
+            float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (m < g.M) x = *reinterpret_cast<const float4 *>(A + m * K2 + k4);
+            const float xs[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int kk = k4 + q;
+                const uint32_t off = (uint32_t)((kk / KC) * TC_BM * 128) + sw128(r, (kk % KC) * ESZ);
+                if constexpr (KIND == 0) {
+                    float hi, lo;
+                    split_tf32(xs[q], hi, lo);
+                    *reinterpret_cast<float *>(sA[st][0] + off) = hi;
+                    *reinterpret_cast<float *>(sA[st][1] + off) = lo;
+                } else {
+                    __nv_bfloat16 hi, lo;
+                    split_bf16(xs[q], hi, lo);
+                    *reinterpret_cast<__nv_bfloat16 *>(sA[st][0] + off) = hi;
+                    if constexpr (X3) *reinterpret_cast<__nv_bfloat16 *>(sA[st][1] + off) = lo;
+                }
+            }
+        }
+        // K padding of the last row block stays zero from the first fill
+    };
+    auto issue = [&](int st, int acc) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n");
+        const uint32_t d = tmem + (uint32_t)(acc * nbp);
+        const int nks = (K2 + KSTEP - 1) / KSTEP;  // K steps covering 2K (padding is zero)
+        for (int ks = 0; ks < nks; ++ks) {
+            const uint32_t kb = (uint32_t)((ks * KSTEP) / KC);
+            const uint32_t ko = (uint32_t)(((ks * KSTEP) % KC) * ESZ);
+            const uint64_t ahi = make_desc(smem_u32(sA[st][0]) + kb * TC_BM * 128 + ko);
+            const uint64_t bhi = make_desc(smem_u32(sB[0]) + kb * nbp * 128 + ko);
+            mma<KIND>(d, ahi, bhi, idesc, ks == 0 ? 0u : 1u);
+            if constexpr (X3) {
+                const uint64_t alo = make_desc(smem_u32(sA[st][1]) + kb * TC_BM * 128 + ko);
+                const uint64_t blo = make_desc(smem_u32(sB[1]) + kb * nbp * 128 + ko);
+                mma<KIND>(d, ahi, blo, idesc, 1u);
+                mma<KIND>(d, alo, bhi, idesc, 1u);
+            }
+        }
+        asm volatile(
+            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                smem_u32(&bars[acc])));
+    };
+    auto epilogue = [&](int64_t t, int acc) {
+        const int64_t item = t / mtiles, m0 = (t % mtiles) * TC_BM;
+        float *C = g.C + item * g.sC;
+        const int64_t row = m0 + warp * 32 + (tid & 31);
+        for (int c0 = 0; c0 < nbp; c0 += 16) {
+            uint32_t v[16];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(acc * nbp + c0);
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+                "%13,%14,%15}, [%16];\n"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                  "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
+                  "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+            if (row < g.M) {
+                if (c0 + 16 <= N2 && (N2 & 3) == 0) {
+#pragma unroll
+                    for (int q = 0; q < 16; q += 4)
+                        *reinterpret_cast<float4 *>(C + row * N2 + c0 + q) =
+                            make_float4(__uint_as_float(v[q]), __uint_as_float(v[q + 1]),
+                                        __uint_as_float(v[q + 2]), __uint_as_float(v[q + 3]));
+                } else {
+                    for (int q = 0; q < 16 && c0 + q < N2; ++q) C[row * N2 + c0 + q] = __uint_as_float(v[q]);
+                }
+            }
+        }
+    };
+
+    // zero both stages once (K padding of partially filled row blocks)
+    for (int i = tid; i < (int)((X3 ? 4 : 2) * a_part / 16); i += TC_THREADS)
+        reinterpret_cast<int4 *>(sm)[i] = make_int4(0, 0, 0, 0);
+    int64_t t = blockIdx.x;
+    int64_t cur_item = -1;
+    bool item_valid = true;
+    if (t < n_tiles) {
+        cur_item = t / mtiles;
+        const float *B = b_src(cur_item, item_valid);
+        if (item_valid) build_b(B);
+        load_a(t, 0);
+    }
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    __syncthreads();
+    if (t < n_tiles && item_valid && tid == 0) issue(0, 0);
+    int it = 0;
+    while (t < n_tiles && ok) {
+        const int st = it & 1, acc = it & 1;
+        const int64_t tn = t + gridDim.x;
+        const bool more = tn < n_tiles;
+        const bool valid_now = item_valid;
+        if (more) load_a(tn, st ^ 1);
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
+        if (valid_now) {
+            ok = mbar_wait(smem_u32(&bars[acc]), phase[acc]);
+            phase[acc] ^= 1u;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;\n");
+        if (more && ok) {
+            const int64_t ni = tn / mtiles;
+            if (ni != cur_item) {  // B of a new batch item (its MMAs are done)
+                cur_item = ni;
+                const float *B = b_src(ni, item_valid);
+                if (item_valid) build_b(B);
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                __syncthreads();
+            }
+            if (item_valid && tid == 0) issue(st ^ 1, acc ^ 1);
+        }
+        if (ok && valid_now) epilogue(t, acc);
+        asm volatile("tcgen05.fence::before_thread_sync;\n");
+        __syncthreads();
+        t = tn;
+        ++it;
+    }
+    if (!ok) {
+        if (tid == 0) atomicExch(g.err, 5);
+        mbar_wait(smem_u32(&bars[0]), phase[0]);
+        mbar_wait(smem_u32(&bars[1]), phase[1]);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(ncols));
+}
+
+size_t tc_persistent_smem(int prec, int K2, int N2) {
+    const bool x3 = prec != 3;
+    const int esz = prec == 1 ? 4 : 2;
+    const int kc = 128 / esz;
+    const int kblocks = (K2 + kc - 1) / kc;
+    const int nbp = (N2 + 15) & ~15;
+    return 1024 + (size_t)kblocks * TC_BM * 128 * 2 * (x3 ? 2 : 1) + (size_t)kblocks * nbp * 128 * 2;
+}
+
 size_t tc_smem_bytes(int prec) {
     const bool x3 = prec != 3;
     return 1024 + (size_t)TC_BM * 128 * (x3 ? 2 : 1) + (size_t)TC_MAX_N2 * 128 * 2;
@@ -309,6 +559,32 @@ cudaError_t run_tc(const TcArgs &a0, int64_t batch, tn_precision prec, cudaStrea
     TcArgs a = a0;
     if (!g_tc_err) return cudaErrorInitializationError;  // tc_gemm_init() not called
     a.err = g_tc_err;
+    const int K2 = 2 * a.K, N2 = 2 * a.N;
+    if (K2 <= P_K2MAX && K2 % 4 == 0 && N2 <= TC_MAX_N2 && batch <= 65535 &&
+        tc_persistent_smem((int)prec, K2, N2) <= P_SMEM_MAX) {
+        static int num_sms = 0;
+        if (!num_sms) {
+            int dev;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
+        }
+        const int64_t tiles = ((a.M + TC_BM - 1) / TC_BM) * batch;
+        const size_t smem = tc_persistent_smem((int)prec, K2, N2);
+        // as many resident blocks per SM as shared memory allows (at most 4;
+        // each holds 2 x 2N <= 512 TMEM columns in total)
+        int per_sm = (int)std::max<size_t>(1, std::min<size_t>(4, (228 * 1024) / (smem + 1024)));
+        int ncols = 32;
+        while (ncols < 2 * ((N2 + 15) & ~15)) ncols <<= 1;
+        per_sm = std::max(1, std::min(per_sm, 512 / ncols));  // TMEM: 512 columns per SM
+        const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)num_sms * per_sm));
+        switch (prec) {
+            case TN_PREC_TF32x3: tc_cgemm_persistent<1><<<grid, TC_THREADS, smem, st>>>(a, batch); break;
+            case TN_PREC_BF16x3: tc_cgemm_persistent<2><<<grid, TC_THREADS, smem, st>>>(a, batch); break;
+            case TN_PREC_BF16x1: tc_cgemm_persistent<3><<<grid, TC_THREADS, smem, st>>>(a, batch); break;
+            default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
     const int64_t gx = (a.M + TC_BM - 1) / TC_BM;
     const int gz = (2 * a.N + TC_MAX_N2 - 1) / TC_MAX_N2;
     if (gx > 0x7fffffffLL || batch > 65535 || gz > 65535) return cudaErrorInvalidValue;
@@ -341,6 +617,17 @@ cudaError_t tc_gemm_init() {
         e = cudaFuncSetAttribute(tc_cgemm_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem3);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(tc_cgemm_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem1);
+    int optin = 0, dev = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) P_SMEM_MAX = (size_t)optin - 2048;
+    const int pmax = (int)P_SMEM_MAX;
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(tc_cgemm_persistent<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, pmax);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(tc_cgemm_persistent<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, pmax);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(tc_cgemm_persistent<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, pmax);
     if (e == cudaSuccess && !g_tc_err) e = cudaGetSymbolAddress((void **)&g_tc_err, g_tc_err_flag);
     return e;
 }

@@ -92,7 +92,8 @@ TC_TOL = {"tf32x3": 1e-5, "bf16x3": 1e-4, "bf16x1": 1e-2}
 @pytest.mark.parametrize("prec", ["tf32x3", "bf16x3", "bf16x1"])
 @pytest.mark.parametrize("M,K,N,batch", [(128, 16, 8, 1), (1000, 4, 8, 1), (4096, 16, 16, 2),
                                          (777, 64, 64, 1), (333, 3, 5, 3), (300, 128, 128, 1),
-                                         (256, 32, 200, 1), (1, 1, 1, 1)])
+                                         (256, 32, 200, 1), (1, 1, 1, 1), (100000, 32, 96, 1),
+                                         (50000, 8, 4, 3), (70001, 2, 2, 2), (9999, 16, 9, 1)])
 def test_cgemm_tensor_core_matches_fp64(prec, M, K, N, batch):
     A = random_complex((batch, M, K), 21, np.complex64)
     B = random_complex((batch, K, N), 22, np.complex64)
