@@ -310,11 +310,17 @@ def _closed_form(c, oq, closed_bits, sliced_by_wire, slice_id):
     return scal * out, scale
 
 
-@pytest.mark.parametrize("name", ["diag53_m14", "diag53_m12"])
-def test_full_size_plan_identity_fsim_closed_form(name):
+@pytest.mark.parametrize("name,n_open", [("diag53_m14", None), ("diag53_m12", None),
+                                         ("diag53_m12", 0), ("diag53_m12", 4), ("diag53_m12", 8)])
+def test_full_size_plan_identity_fsim_closed_form(name, n_open):
+    # the 53-qubit 12-cycle workload is also run at 1, 16 and 256 amplitudes
+    # per batch (0, 4, 8 open qubits) beside its 64-amplitude default
     from bench import plan_options, workload_inputs
     cfg = CONFIGS[name]
     c, oq, cb_bench = workload_inputs(name)
+    if n_open is not None:
+        oq = c.layout.open_qubits(n_open)
+        cb_bench = list(random_bits(c.n_qubits - n_open, cfg["bit_seed"]))
     c0 = Circuit(c.n_qubits, c.n_cycles, c.gates_1q, c.pairs, 0.0, 0.0, c.layout)
     closed = [q for q in range(c.n_qubits) if q not in set(oq)]
     v0 = _qubit_vectors(c0, {}, 0)
