@@ -136,6 +136,14 @@ tn_status tn_build_network(const tn_circuit *c, const int32_t *open_qubits, int3
 tn_status tn_network_info(const tn_network *net, int32_t *n_leaves, int32_t *n_edges,
                           int32_t *qubit, int32_t *segment);
 
+/* Sec. 3: re-value the closed-qubit projectors <b| of net with a new prefix
+ * (n_qubits - n_open bytes, 0/1; else TN_ERR_INVALID_ARG and net unchanged).
+ * The network's structure is kept, so an order or sliced set found for it
+ * stays valid. Plans copy the network when created: a plan made before this
+ * call keeps its old prefix (tn_plan_prepare takes explicit prefixes). Host
+ * only. */
+tn_status tn_set_prefix(tn_network *net, const uint8_t *closed_bits);
+
 /* Supp. A.1-A.2: make a contraction scheme. order (n_pairs = n_leaves - 1
  * SSA pairs) may be NULL: the planner then grows a stem (Sec. 4). sliced_edges
  * may be NULL: the planner then slices greedily (Supp. A.2, "Dynamic slicing")
@@ -212,8 +220,13 @@ tn_status tn_plan_profile(tn_plan *plan, uint64_t slice_begin, tn_precision prec
 tn_status tn_contract_stem_noalloc(tn_plan *plan, uint64_t slice_begin, uint64_t slice_end,
                                    void *cuda_stream, double *amps_out, int32_t accumulate);
 
+/* Free a handle (NULL is a no-op). tn_destroy_plan / tn_destroy_network are
+ * the same calls under their short names. Synchronise the stream that used
+ * a plan before destroying it. */
 void tn_plan_destroy(tn_plan *plan);
 void tn_network_destroy(tn_network *net);
+void tn_destroy_plan(tn_plan *plan);
+void tn_destroy_network(tn_network *net);
 
 /* ---- learned step-time cost model and plan search (no counterpart in the
  * paper, whose order search is KaHyPar + CMA-ES; here candidate plans are

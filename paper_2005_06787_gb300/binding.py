@@ -31,7 +31,7 @@ EXPORTED = [
     "tn_network_destroy", "tn_linear_xeb", "tn_permute", "tn_cgemm", "tn_last_error",
     "tn_version", "tn_plan_features", "tn_mlp_create", "tn_mlp_n_params", "tn_mlp_set_params",
     "tn_mlp_get_params", "tn_mlp_loss_grad", "tn_mlp_train", "tn_mlp_predict", "tn_mlp_destroy",
-    "tn_plan_search",
+    "tn_plan_search", "tn_set_prefix", "tn_destroy_plan", "tn_destroy_network",
 ]
 N_FEATURES = 16
 
@@ -115,6 +115,11 @@ def load():
     L.tn_plan_destroy.argtypes = [vp]
     L.tn_plan_destroy.restype = None
     L.tn_network_destroy.argtypes = [vp]
+    L.tn_destroy_plan.argtypes = [vp]
+    L.tn_destroy_plan.restype = None
+    L.tn_destroy_network.argtypes = [vp]
+    L.tn_destroy_network.restype = None
+    L.tn_set_prefix.argtypes = [vp, vp]
     L.tn_network_destroy.restype = None
     L.tn_plan_profile.argtypes = [vp, u64, C.c_int, C.c_int, vp, vp, i32, vp]
     L.tn_linear_xeb.argtypes = [vp, i64, i32, vp, C.POINTER(C.c_double)]
@@ -138,7 +143,7 @@ def load():
     L.tn_version.argtypes = []
     for name in EXPORTED:
         if name not in ("tn_plan_destroy", "tn_network_destroy", "tn_last_error", "tn_version",
-                        "tn_mlp_destroy"):
+                        "tn_mlp_destroy", "tn_destroy_plan", "tn_destroy_network"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -212,6 +217,16 @@ def tn_build_network(circuit, open_qubits: Sequence[int], closed_bits: Sequence[
     return Network(h, len(open_qubits), circuit.n_qubits - len(open_qubits), (g, offs, pairs))
 
 
+def tn_set_prefix(net: Network, closed_bits: Sequence[int]) -> None:
+    """Re-value the network's closed-qubit projectors with a new prefix."""
+    L = load()
+    cb = np.asarray(list(closed_bits), dtype=np.uint8)
+    if cb.size != net.n_closed:
+        raise ValueError(f"expected {net.n_closed} closed bits, got {cb.size}")
+    cb = np.ascontiguousarray(cb if cb.size else np.zeros(1, np.uint8))
+    _check(L.tn_set_prefix(net.handle, cb.ctypes.data))
+
+
 # ------------------------------------------------------------------------ plan
 
 def make_opts(**kw) -> tn_plan_opts:
@@ -255,6 +270,20 @@ def tn_plan_create(net: Network, order: Optional[Sequence[Tuple[int, int]]] = No
     _check(L.tn_plan_create(net.handle, _ptr(ordp) or None, n_pairs, _ptr(slp) or None, nsl,
                             C.byref(o), C.byref(h)))
     return Plan(h, net)
+
+
+def tn_destroy_plan(plan: Plan) -> None:
+    """Free a plan now (otherwise it is freed when garbage-collected)."""
+    if plan.handle:
+        load().tn_destroy_plan(plan.handle)
+        plan.handle = None
+
+
+def tn_destroy_network(net: Network) -> None:
+    """Free a network now (plans made from it hold their own copy)."""
+    if net.handle:
+        load().tn_destroy_network(net.handle)
+        net.handle = None
 
 
 def tn_plan_prepare(plan: Plan, prefixes: Optional[np.ndarray] = None, stream=None):

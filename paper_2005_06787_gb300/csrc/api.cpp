@@ -342,6 +342,15 @@ tn_status tn_plan_search(tn_network *net, const tn_plan_opts *base, const tn_sea
 
 void tn_plan_destroy(tn_plan *plan) { delete plan; }
 void tn_network_destroy(tn_network *net) { delete net; }
+void tn_destroy_plan(tn_plan *plan) { delete plan; }
+void tn_destroy_network(tn_network *net) { delete net; }
+
+tn_status tn_set_prefix(tn_network *net, const uint8_t *closed_bits) {
+    return guard([&] {
+        if (!net) tn::fail(TN_ERR_INVALID_ARG, "null network");
+        tn::set_prefix(net->net, closed_bits);
+    });
+}
 
 tn_status tn_linear_xeb(const double *amps_dev, int64_t count, int32_t n_qubits,
                         void *cuda_stream, double *out) {

@@ -124,6 +124,9 @@ struct Network {
 
 Network build_network(const tn_circuit &c, const int32_t *open_qubits, int n_open,
                       const uint8_t *closed_bits);
+// Re-value the closed-qubit projectors (Sec. 3 post-selection); the structure,
+// and so any plan made from it, is unchanged.
+void set_prefix(Network &net, const uint8_t *closed_bits);
 void gate_matrix_1q(int id, cd out[4]);
 void fsim_matrix(double theta, double phi, cd out[16]);
 

@@ -151,4 +151,17 @@ Network build_network(const tn_circuit &c, const int32_t *open_qubits, int n_ope
     return net;
 }
 
+void set_prefix(Network &net, const uint8_t *closed_bits) {
+    if (!net.closed_qubits.empty() && !closed_bits) fail(TN_ERR_INVALID_ARG, "closed_bits is null");
+    for (size_t i = 0; i < net.closed_qubits.size(); ++i)
+        if (closed_bits[i] > 1) fail(TN_ERR_INVALID_ARG, "closed bits must be 0 or 1");
+    for (size_t i = 0; i < net.closed_qubits.size(); ++i) {
+        const int b = closed_bits[i];
+        net.closed_bits[i] = (uint8_t)b;
+        Leaf &L = net.leaves[(size_t)net.proj_leaf[i]];
+        L.vals[0] = b == 0 ? 1.0 : 0.0;
+        L.vals[1] = b == 1 ? 1.0 : 0.0;
+    }
+}
+
 }  // namespace tn

@@ -231,6 +231,26 @@ def test_prefix_batch_equals_single_prefixes():
         assert rel_l2(got[i], oracle.sv_amplitudes(c, oq, p, psi)) < TOL
 
 
+def test_set_prefix_revalues_projectors_and_short_names():
+    # a plan made after tn_set_prefix contracts the new prefix; one made before
+    # keeps the old one; tn_destroy_* free handles at once
+    c = random_circuit(grid_layout(3, 4), 8, 78)
+    oq = [1, 6]
+    a, b = list(random_bits(10, 401)), list(random_bits(10, 402))
+    net = P.tn_build_network(c, oq, a)
+    plan_a = P.tn_plan_create(net, cw_limit=6, restarts=2)
+    P.tn_set_prefix(net, b)
+    plan_b = P.tn_plan_create(net, cw_limit=6, restarts=2)
+    psi = oracle.statevector(c)
+    for plan, bits in ((plan_a, a), (plan_b, b)):
+        P.tn_plan_prepare(plan)
+        got = run(plan, 0, 1 << P.tn_plan_info(plan)["n_sliced"])[0]
+        assert rel_l2(got, oracle.sv_amplitudes(c, oq, bits, psi)) < TOL
+    P.tn_destroy_plan(plan_a)
+    P.tn_destroy_plan(plan_b)
+    P.tn_destroy_network(net)
+
+
 # ------------------------------------------------------------ 30-qubit grid
 
 def test_grid5x6_m14_against_stored_statevector():

@@ -34,6 +34,20 @@ def test_library_exports_every_header_symbol():
     assert set(P.EXPORTED) <= declared
 
 
+def test_set_prefix_rejects_bad_bits():
+    c = random_circuit(grid_layout(2, 3), 4, 9)
+    net = P.tn_build_network(c, [0], [0, 1, 0, 1, 1])
+    with pytest.raises(P.TnError):
+        P.tn_set_prefix(net, [0, 1, 2, 1, 1])
+    with pytest.raises(ValueError):
+        P.tn_set_prefix(net, [0, 1])
+    P.tn_set_prefix(net, [1, 1, 0, 0, 1])
+    plan = P.tn_plan_create(net, cw_limit=6, restarts=1)
+    assert P.tn_plan_info(plan)["cw"] <= 6
+    P.tn_destroy_plan(plan)
+    P.tn_destroy_network(net)
+
+
 def _net(c, oq, seed):
     cb = list(random_bits(c.n_qubits - len(oq), seed))
     return P.tn_build_network(c, oq, cb), cb
