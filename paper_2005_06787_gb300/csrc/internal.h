@@ -191,14 +191,19 @@ inline int tile_swizzle(int p) {
 }
 
 // All offsets are in complex elements; tile offsets are swizzled positions.
+// Steps run in place: a step reads the 2^k entries of each rest index at
+// lo/hi(rest) ^ koff[kappa] and writes its 2^n results at lo/hi(rest) ^
+// noff[nu] in the same buffer. Rest bits keep their tile positions; the nu
+// bits take the positions the kappa bits held, then free ones. The write set
+// of a rest index holds its read set or lies inside it, and different rest
+// indices touch disjoint entries, so no entry is read after another thread
+// wrote it within a step.
 struct alignas(16) DevStep {
     int k, n, rest;
-    int branch;                 // index into DevBranch table
+    int branch;                 // index into DevBranch table (-1: no step)
     int koff[16], noff[16];     // tile offsets of kappa / nu bits
-    int in_lo[64], in_hi[64];   // rest index -> input tile offset
-    int out_lo[64], out_hi[64]; // rest index -> output tile offset
+    int lo[64], hi[64];         // rest index bits 0-5 / 6-11 -> tile offset
 };
-
 struct DevBranch {
     int64_t base;           // offset into the branch pool
     int64_t prefix_stride;  // 0 when independent of the prefix
@@ -221,6 +226,7 @@ struct alignas(16) DevPass {
     int64_t n_tiles;        // 2^n_free
     int chunk_in_base, chunk_out_base;  // offsets into the chunk table
     int64_t free_in[MAX_FREE], free_out[MAX_FREE];  // strides of free bits
+    int st_lo[64], st_hi[64];  // tile-out index bits 0-5 / 6-11 -> tile offset
     DevStep steps[MAX_PASS_STEPS];
 };
 static_assert(sizeof(DevPass) % 16 == 0, "DevPass must be a multiple of 16 bytes");

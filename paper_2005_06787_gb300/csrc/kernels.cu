@@ -36,19 +36,17 @@ __device__ __forceinline__ int dev_swizzle(int p) {
     return p ^ a ^ (((b << 2) | (b >> 2)) & 15);
 }
 
-// One stem step inside the tile: for each rest index rho (thread-strided),
-// y[nu] = sum_kappa x[kappa] * B[kappa][nu], read at in-tile offsets
-// io(rho) + koff[kappa], written at oo(rho) + noff[nu].
-// One stem step on the tile: for each rest index rho (one per thread and
-// iteration), y[nu] = sum_kappa x[kappa] * B[kappa][nu], read at in-tile
-// offsets io(rho) ^ koff[kappa], written at oo(rho) ^ noff[nu]. Branch
-// clusters have rank <= 4, so B (2^(K+N) <= 16 entries) and both offset lists
-// live in registers for the whole step. The thread count is a power of two
-// >= 64, so the low six bits of rho are fixed per thread and only the high
-// half of each offset table is read per iteration.
+// One stem step on the tile, in place: for each rest index rho (one per
+// thread and iteration), y[nu] = sum_kappa x[kappa] * B[kappa][nu], reading
+// x at t(rho) ^ koff[kappa] and writing y at t(rho) ^ noff[nu]. A thread
+// reads all of its x before writing, and different rest indices touch
+// disjoint entries. Branch clusters have rank <= 4, so B (2^(K+N) <= 16
+// entries) and both offset lists live in registers for the whole step. The
+// thread count is a power of two >= 64, so rest-index bits 0-5 are fixed per
+// thread and only the high table is read per iteration.
 template <int K, int N>
-__device__ __forceinline__ void step_body(const float2 *__restrict__ tin, float2 *__restrict__ tout,
-                                          const DevStep &S, const float2 *__restrict__ Bm, int nt) {
+__device__ __forceinline__ void step_body(float2 *tile, const DevStep &S, const float2 *__restrict__ Bm,
+                                          int nt) {
     constexpr int NK = 1 << K, NN = 1 << N;
     float2 bv[NK * NN];
 #pragma unroll
@@ -59,41 +57,26 @@ __device__ __forceinline__ void step_body(const float2 *__restrict__ tin, float2
 #pragma unroll
     for (int nn = 0; nn < NN; ++nn) noff[nn] = S.noff[nn];
     const int nrest = 1 << S.rest;
-    const int io_lo = S.in_lo[threadIdx.x & 63], oo_lo = S.out_lo[threadIdx.x & 63];
+    const int t_lo = S.lo[threadIdx.x & 63];
     for (int r = threadIdx.x; r < nrest; r += nt) {
-        const int io = io_lo ^ S.in_hi[r >> 6];
-        const int oo = oo_lo ^ S.out_hi[r >> 6];
+        const int t = t_lo ^ S.hi[r >> 6];
         float2 x[NK];
 #pragma unroll
-        for (int kk = 0; kk < NK; ++kk) x[kk] = tin[io ^ koff[kk]];
+        for (int kk = 0; kk < NK; ++kk) x[kk] = tile[t ^ koff[kk]];
 #pragma unroll
         for (int nn = 0; nn < NN; ++nn) {
             float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
             for (int kk = 0; kk < NK; ++kk) cfma(acc, x[kk], bv[kk * NN + nn]);
-            tout[oo ^ noff[nn]] = acc;
+            tile[t ^ noff[nn]] = acc;
         }
     }
 }
 
-// Identity step of a pure permutation pass.
-__device__ __forceinline__ void copy_body(const float2 *__restrict__ tin, float2 *__restrict__ tout,
-                                          const DevStep &S, int nt) {
-    const int nrest = 1 << S.rest;
-    const int io_lo = S.in_lo[threadIdx.x & 63], oo_lo = S.out_lo[threadIdx.x & 63];
-    for (int r = threadIdx.x; r < nrest; r += nt)
-        tout[oo_lo ^ S.out_hi[r >> 6]] = tin[io_lo ^ S.in_hi[r >> 6]];
-}
-
-__device__ void run_step(const float2 *tin, float2 *tout, const DevStep &S, const float2 *Bm,
-                         int nt) {
-    if (S.branch < 0) {
-        copy_body(tin, tout, S, nt);
-        return;
-    }
+__device__ void run_step(float2 *tile, const DevStep &S, const float2 *Bm, int nt) {
     switch (S.k * 8 + S.n) {
 #define TN_CASE(K, N) \
-    case K * 8 + N: step_body<K, N>(tin, tout, S, Bm, nt); break;
+    case K * 8 + N: step_body<K, N>(tile, S, Bm, nt); break;
         TN_CASE(1, 0) TN_CASE(1, 1) TN_CASE(1, 2) TN_CASE(1, 3)
         TN_CASE(2, 0) TN_CASE(2, 1) TN_CASE(2, 2)
         TN_CASE(3, 0) TN_CASE(3, 1)
@@ -103,12 +86,27 @@ __device__ void run_step(const float2 *tin, float2 *tout, const DevStep &S, cons
     }
 }
 
+// Asynchronous 8-byte global -> shared copy (Ampere-style cp.async; the
+// tile's bank swizzle permutes single entries, so copies are entry-sized).
+__device__ __forceinline__ void cp_async8(void *smem_dst, const void *gmem_src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() {
+    asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 constexpr int PASS_THREADS = 256;
 constexpr size_t PASS_HEAD_BYTES = (offsetof(DevPass, steps) + 15) / 16 * 16;
 
-// A fused pass over batch items x tiles, one tile per block iteration: load
-// the tile (16-byte loads of contiguous chunks, swizzled into shared memory),
-// apply the pass's stem steps, store the tile in the next layout.
+// A fused pass over batch items x tiles. Each block walks its tiles with two
+// tile buffers: while the steps run in place on one tile, the next tile's
+// entries stream into the other buffer with cp.async, so the HBM read of
+// tile i+1 overlaps the arithmetic of tile i. A tile's load puts input tile
+// edge i at tile position i; the store reads the final positions through the
+// st_lo / st_hi tables and writes the next layout.
 // Shared memory: pass header and used step tables | chunk tables | two tiles
 // | branch matrices of the current batch item.
 template <int MINB>
@@ -130,9 +128,10 @@ pass_kernel(const DevPass *__restrict__ gpass, const int *__restrict__ chunks,
     int *cin_tab = reinterpret_cast<int *>(smem + head);
     const int n_cin = 1 << (P.t_in - P.c_in), n_cout = 1 << (P.t_out - P.c_out);
     int *cout_tab = cin_tab + n_cin;
-    float2 *tA = reinterpret_cast<float2 *>(smem + head + (size_t)((n_cin + n_cout + 3) & ~3) * 4);
-    float2 *tB = tA + P.tile_max;
-    float2 *bm = tB + P.tile_max;
+    // tile buffer b (0 or 1) starts at tbuf + b * tile_max
+    float2 *tbuf = reinterpret_cast<float2 *>(smem + head + (size_t)((n_cin + n_cout + 3) & ~3) * 4);
+    const int tile_max = P.tile_max;
+    float2 *bm = tbuf + 2 * tile_max;
     for (int i = threadIdx.x; i < n_cin; i += PASS_THREADS) cin_tab[i] = chunks[P.chunk_in_base + i];
     for (int i = threadIdx.x; i < n_cout; i += PASS_THREADS) cout_tab[i] = chunks[P.chunk_out_base + i];
     auto bm_off = [&](int t) {
@@ -152,16 +151,41 @@ pass_kernel(const DevPass *__restrict__ gpass, const int *__restrict__ chunks,
     // this lane's free bit (free bits are disjoint, so offsets combine with OR)
     const unsigned my_fin = lane < (unsigned)nfree ? (unsigned)P.free_in[lane] : 0u;
     const unsigned my_fout = lane < (unsigned)nfree ? (unsigned)P.free_out[lane] : 0u;
+    const int st_lo = P.st_lo[threadIdx.x & 63];
     __syncthreads();
-    int last_item = -1;
-    for (int64_t u = blockIdx.x; u < n_units; u += gridDim.x) {
-        const int item = (int)(u >> nfree);
-        const unsigned tile = (unsigned)(u & (P.n_tiles - 1));
+    // unit u -> (batch item, prefix, slice); invalid past the slice range
+    auto unit_item = [&](int64_t u, int &item, int &p, int64_t &s) {
+        item = (int)(u >> nfree);
         const int pl = item / ba.SB;
-        const int p = ba.p0 + pl;
-        const int64_t s = base + (item - pl * ba.SB);
-        if (s >= send) continue;  // uniform over the block
-        if (item != last_item) {
+        p = ba.p0 + pl;
+        s = base + (item - pl * ba.SB);
+        return s < send;
+    };
+    // issue the cp.async copies of unit u's input tile into buffer dstb
+    auto issue_load = [&](int64_t u, float2 *dstb) {
+        int item, p;
+        int64_t s;
+        if (!unit_item(u, item, p, s)) return;
+        const unsigned tile = (unsigned)(u & (P.n_tiles - 1));
+        const unsigned ib = __reduce_or_sync(0xffffffffu, ((tile >> lane) & 1u) ? my_fin : 0u);
+        const float2 *src = (P.in_branch >= 0) ? pool + branch_offset(branches[P.in_branch], p, s)
+                                               : in + (int64_t)item * P.in_item_stride;
+        src += ib;
+        for (int idx = threadIdx.x; idx < tin_n; idx += PASS_THREADS)
+            cp_async8(dstb + dev_swizzle(idx), src + cin_tab[idx >> c_in] + (idx & cin_mask));
+    };
+    int last_item = -1;
+    int buf = 0;
+    if ((int64_t)blockIdx.x < n_units) issue_load(blockIdx.x, tbuf);
+    cp_async_commit();
+    for (int64_t u = blockIdx.x; u < n_units; u += gridDim.x, buf ^= 1) {
+        if (u + gridDim.x < n_units) issue_load(u + gridDim.x, tbuf + (buf ^ 1) * tile_max);
+        cp_async_commit();
+        cp_async_wait_prev();
+        int item, p;
+        int64_t s;
+        const bool valid = unit_item(u, item, p, s);  // uniform over the block
+        if (valid && item != last_item) {
             for (int t = 0; t < P.n_steps; ++t) {
                 const int br = P.steps[t].branch;
                 if (br < 0) continue;
@@ -172,49 +196,23 @@ pass_kernel(const DevPass *__restrict__ gpass, const int *__restrict__ chunks,
             }
             last_item = item;
         }
-        const bool mine = (tile >> lane) & 1u;
-        const unsigned ib = __reduce_or_sync(0xffffffffu, mine ? my_fin : 0u);
-        const unsigned ob = __reduce_or_sync(0xffffffffu, mine ? my_fout : 0u);
-        const float2 *src;
-        if (P.in_branch >= 0)
-            src = pool + branch_offset(branches[P.in_branch], p, s);
-        else
-            src = in + (int64_t)item * P.in_item_stride;
-        src += ib;
-        float2 *dst = out + (int64_t)item * P.out_item_stride + ob;
-        if (c_in >= 1) {
-            for (int idx = threadIdx.x * 2; idx < tin_n; idx += PASS_THREADS * 2) {
-                const float4 v = *reinterpret_cast<const float4 *>(src + cin_tab[idx >> c_in] + (idx & cin_mask));
-                const int ph = dev_swizzle(idx);
-                tA[ph] = make_float2(v.x, v.y);
-                tA[ph ^ 1] = make_float2(v.z, v.w);
-            }
-        } else {
-            for (int idx = threadIdx.x; idx < tin_n; idx += PASS_THREADS)
-                tA[dev_swizzle(idx)] = src[cin_tab[idx]];
-        }
         __syncthreads();
-        float2 *cur = tA, *nxt = tB;
-        for (int t = 0; t < P.n_steps; ++t) {
-            run_step(cur, nxt, P.steps[t], bm + bm_off(t), PASS_THREADS);
-            __syncthreads();
-            float2 *tmp = cur;
-            cur = nxt;
-            nxt = tmp;
-        }
-        if (c_out >= 1) {
-            for (int idx = threadIdx.x * 2; idx < tout_n; idx += PASS_THREADS * 2) {
-                const int ph = dev_swizzle(idx);
-                const float2 a = cur[ph], b = cur[ph ^ 1];
-                *reinterpret_cast<float4 *>(dst + cout_tab[idx >> c_out] + (idx & cout_mask)) =
-                    make_float4(a.x, a.y, b.x, b.y);
+        if (valid) {
+            float2 *tile = tbuf + buf * tile_max;
+            for (int t = 0; t < P.n_steps; ++t) {
+                if (P.steps[t].branch < 0) continue;
+                run_step(tile, P.steps[t], bm + bm_off(t), PASS_THREADS);
+                __syncthreads();
             }
-        } else {
+            const unsigned tl = (unsigned)(u & (P.n_tiles - 1));
+            const unsigned ob = __reduce_or_sync(0xffffffffu, ((tl >> lane) & 1u) ? my_fout : 0u);
+            float2 *dst = out + (int64_t)item * P.out_item_stride + ob;
             for (int idx = threadIdx.x; idx < tout_n; idx += PASS_THREADS)
-                dst[cout_tab[idx]] = cur[dev_swizzle(idx)];
+                dst[cout_tab[idx >> c_out] + (idx & cout_mask)] = tile[st_lo ^ P.st_hi[idx >> 6]];
         }
         __syncthreads();
     }
+    cp_async_wait_all();
 }
 
 static size_t pass_smem_bytes(const DevPass &P) {

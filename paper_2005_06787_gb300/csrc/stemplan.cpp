@@ -58,53 +58,75 @@ std::vector<int> sort_by_next_use(std::vector<int> edges, const std::vector<Step
     return edges;
 }
 
-void fill_tables(DevStep &st, const std::vector<int> &lam_in, const std::vector<int> &lam_out,
-                 const std::vector<int> &K, const std::vector<int> &N) {
-    std::vector<int> rest;
-    for (int e : lam_in)
-        if (std::find(K.begin(), K.end(), e) == K.end()) rest.push_back(e);
-    st.k = (int)K.size();
-    st.n = (int)N.size();
+// Bank pair (low four bits of the swizzled offset) that a one-bit stride at
+// tile position q lands on.
+int bank_vec(int q) { return tile_swizzle(1 << q) & 15; }
+
+// Order a step's rest edges into rest-index bits. Rest-index bits 0-3 vary
+// across the 16 lanes of a half-warp; they get edges whose bank vectors are
+// independent over GF(2) where the tile allows, so every half-warp's 8-byte
+// accesses fall on 16 distinct bank pairs. The others follow by position.
+std::vector<int> order_rest(std::vector<int> rest, const std::map<int, int> &pos) {
+    std::sort(rest.begin(), rest.end(), [&](int a, int b) { return pos.at(a) < pos.at(b); });
+    std::vector<int> lanes, others;
+    uint32_t span = 1;  // bit v set: vector v is in the span of the chosen vectors
+    for (int e : rest) {
+        const int v = bank_vec(pos.at(e));
+        if ((int)lanes.size() < 4 && v != 0 && !((span >> v) & 1u)) {
+            lanes.push_back(e);
+            uint32_t add = 0;
+            for (int x = 0; x < 16; ++x)
+                if ((span >> x) & 1u) add |= 1u << (x ^ v);
+            span |= add;
+        } else {
+            others.push_back(e);
+        }
+    }
+    lanes.insert(lanes.end(), others.begin(), others.end());
+    return lanes;
+}
+
+// Tables of one in-place step: kappa offsets at the positions before the
+// step, nu offsets at the positions after it, rest offsets (unchanged).
+void fill_step(DevStep &st, const std::vector<int> &rest, const std::vector<int> &kpos,
+               const std::vector<int> &npos, const std::map<int, int> &pos) {
+    st.k = (int)kpos.size();
+    st.n = (int)npos.size();
     st.rest = (int)rest.size();
     if (st.rest > 12) fail(TN_ERR_UNSUPPORTED, "internal: tile rest exceeds 12 bits");
     for (int kk = 0; kk < 16; ++kk) {
         int o = 0;
         for (int b = 0; b < st.k; ++b)
-            if ((kk >> b) & 1) o ^= tile_swizzle(1 << pos_of(lam_in, K[(size_t)b]));
+            if ((kk >> b) & 1) o ^= tile_swizzle(1 << kpos[(size_t)b]);
         st.koff[kk] = (kk < (1 << st.k)) ? o : 0;
     }
     for (int nn = 0; nn < 16; ++nn) {
         int o = 0;
         for (int b = 0; b < st.n; ++b)
-            if ((nn >> b) & 1) o ^= tile_swizzle(1 << pos_of(lam_out, N[(size_t)b]));
+            if ((nn >> b) & 1) o ^= tile_swizzle(1 << npos[(size_t)b]);
         st.noff[nn] = (nn < (1 << st.n)) ? o : 0;
     }
-    for (int half = 0; half < 2; ++half) {
-        for (int v = 0; v < 64; ++v) {
-            int oi = 0, oo = 0;
-            for (int b = 0; b < 6; ++b) {
-                int rb = half * 6 + b;
-                if (rb >= st.rest || !((v >> b) & 1)) continue;
-                int pi = pos_of(lam_in, rest[(size_t)rb]);
-                int po = pos_of(lam_out, rest[(size_t)rb]);
-                if (pi < 0 || po < 0) fail(TN_ERR_UNSUPPORTED, "internal: rest edge lost");
-                oi ^= tile_swizzle(1 << pi);
-                oo ^= tile_swizzle(1 << po);
-            }
-            if (half == 0) {
-                st.in_lo[v] = oi;
-                st.out_lo[v] = oo;
-            } else {
-                st.in_hi[v] = oi;
-                st.out_hi[v] = oo;
-            }
+    for (int v = 0; v < 64; ++v) {
+        int a = 0, b = 0;
+        for (int j = 0; j < 6; ++j) {
+            if (!((v >> j) & 1)) continue;
+            if (j < st.rest) a ^= tile_swizzle(1 << pos.at(rest[(size_t)j]));
+            if (j + 6 < st.rest) b ^= tile_swizzle(1 << pos.at(rest[(size_t)(j + 6)]));
         }
+        st.lo[v] = a;
+        st.hi[v] = b;
     }
 }
 
 // Build a pass from in-layout to out-layout applying `group` steps (indices
 // into steps, with branch ids br). tile_in_edges must contain the low c_in
 // input edges and every input edge the group contracts.
+//
+// The tile is loaded with input tile edge i (by ascending input position) at
+// tile position i. Each step runs in place: rest edges keep their positions,
+// the nu edges take the kappa edges' positions, then the lowest free ones.
+// The store reads the final positions through the st_lo / st_hi tables, so
+// the output layout costs nothing extra.
 DevPass build_pass(const std::vector<int> &Lin, const std::vector<int> &Lout, int c_in, int c_out,
                    const std::set<int> &tile_in_edges, const std::vector<int> &group,
                    const std::vector<StepSets> &steps, const std::vector<int> &branch_of_step,
@@ -115,38 +137,68 @@ DevPass build_pass(const std::vector<int> &Lin, const std::vector<int> &Lout, in
     P.c_in = c_in;
     P.c_out = c_out;
     P.in_branch = -1;
-    // tile-local input layout: tile edges by ascending input position
     std::vector<int> lam_in;
     for (int e : Lin)
         if (tile_in_edges.count(e)) lam_in.push_back(e);
     P.t_in = (int)lam_in.size();
-    // evolve the tile through the group
-    // Intermediate tile states are ordered latest-next-use first: bits that
-    // stay uncontracted occupy the low tile positions, so each step's rest
-    // index (one per thread) walks contiguous, conflict-free positions.
-    std::vector<std::vector<int>> lams{lam_in};
-    std::vector<int> cur = lam_in;
-    for (int s : group) {
-        std::vector<int> nxt;
-        for (int e : cur)
-            if (std::find(steps[(size_t)s].K.begin(), steps[(size_t)s].K.end(), e) ==
-                steps[(size_t)s].K.end())
-                nxt.push_back(e);
-        for (int e : steps[(size_t)s].N) nxt.push_back(e);
-        nxt = sort_by_next_use(nxt, steps, s + 1, true);
-        lams.push_back(nxt);
-        cur = nxt;
+    std::map<int, int> pos;
+    for (size_t i = 0; i < lam_in.size(); ++i) pos[lam_in[i]] = (int)i;
+    int max_t = P.t_in;
+    auto used = [&]() {
+        uint32_t m = 0;
+        for (auto &kv : pos) m |= 1u << kv.second;
+        return m;
+    };
+    if (group.empty()) {
+        P.n_steps = 1;
+        std::vector<int> rest = order_rest(lam_in, pos);
+        fill_step(P.steps[0], rest, {}, {}, pos);
+        P.steps[0].branch = -1;
+    } else {
+        P.n_steps = (int)group.size();
+        for (size_t t = 0; t < group.size(); ++t) {
+            const StepSets &S = steps[(size_t)group[t]];
+            std::vector<int> kpos;
+            for (int e : S.K) {
+                auto it = pos.find(e);
+                if (it == pos.end()) fail(TN_ERR_UNSUPPORTED, "internal: contracted edge not in tile");
+                kpos.push_back(it->second);
+            }
+            std::vector<int> rest;
+            for (auto &kv : pos)
+                if (std::find(S.K.begin(), S.K.end(), kv.first) == S.K.end()) rest.push_back(kv.first);
+            rest = order_rest(rest, pos);
+            for (int e : S.K) pos.erase(e);
+            std::vector<int> free_pos = kpos;
+            const uint32_t occ = used();
+            for (int q = 0; q < 32 && free_pos.size() < S.N.size(); ++q)
+                if (!((occ >> q) & 1u) && std::find(kpos.begin(), kpos.end(), q) == kpos.end())
+                    free_pos.push_back(q);
+            std::vector<int> npos(free_pos.begin(), free_pos.begin() + (long)S.N.size());
+            for (size_t b = 0; b < S.N.size(); ++b) pos[S.N[b]] = npos[b];
+            fill_step(P.steps[t], rest, kpos, npos, pos);
+            P.steps[t].branch = branch_of_step[(size_t)group[t]];
+            max_t = std::max(max_t, (int)pos.size());
+        }
     }
-    std::set<int> tile_out_set(cur.begin(), cur.end());
     // tile-local output layout: tile-out edges by ascending output position
     std::vector<int> lam_out;
     for (int e : Lout)
-        if (tile_out_set.count(e)) lam_out.push_back(e);
-    if (lam_out.size() != cur.size()) fail(TN_ERR_UNSUPPORTED, "internal: tile-out mismatch");
+        if (pos.count(e)) lam_out.push_back(e);
+    if (lam_out.size() != pos.size()) fail(TN_ERR_UNSUPPORTED, "internal: tile-out mismatch");
     P.t_out = (int)lam_out.size();
-    lams.back() = lam_out;
-    P.tile_max = 0;
-    for (auto &l : lams) P.tile_max = std::max(P.tile_max, 1 << (int)l.size());
+    P.tile_max = 1 << max_t;
+    for (int v = 0; v < 64; ++v) {
+        int a = 0, b = 0;
+        for (int j = 0; j < 6; ++j) {
+            if (!((v >> j) & 1)) continue;
+            if (j < P.t_out) a ^= tile_swizzle(1 << pos.at(lam_out[(size_t)j]));
+            if (j + 6 < P.t_out) b ^= tile_swizzle(1 << pos.at(lam_out[(size_t)(j + 6)]));
+        }
+        P.st_lo[v] = a;
+        P.st_hi[v] = b;
+    }
+    std::set<int> tile_out_set(lam_out.begin(), lam_out.end());
     // low c_in input positions must be tile edges; low c_out output positions too
     for (int p = 0; p < c_in; ++p)
         if (!tile_in_edges.count(Lin[(size_t)p])) fail(TN_ERR_UNSUPPORTED, "internal: c_in");
@@ -180,19 +232,6 @@ DevPass build_pass(const std::vector<int> &Lin, const std::vector<int> &Lout, in
             if ((j >> b) & 1) o += 1 << pos_of(Lout, lam_out[(size_t)(c_out + b)]);
         chunk_table.push_back(o);
     }
-    // steps
-    if (group.empty()) {
-        P.n_steps = 1;
-        fill_tables(P.steps[0], lam_in, lam_out, {}, {});
-        P.steps[0].branch = -1;
-    } else {
-        P.n_steps = (int)group.size();
-        for (size_t t = 0; t < group.size(); ++t) {
-            int s = group[t];
-            fill_tables(P.steps[t], lams[t], lams[t + 1], steps[(size_t)s].K, steps[(size_t)s].N);
-            P.steps[t].branch = branch_of_step[(size_t)s];
-        }
-    }
     P.in_item_stride = 1ll << P.r_in;
     P.out_item_stride = 1ll << P.r_out;
     return P;
@@ -200,13 +239,14 @@ DevPass build_pass(const std::vector<int> &Lin, const std::vector<int> &Lout, in
 
 // Check that a pass's descriptors address exactly the tensors they claim:
 // the input (output) bit positions used by chunks, chunk tables and free
-// bits partition [0, r_in) ([0, r_out)), and every tile offset of every step
-// partitions the tile state it reads or writes. Any violation would index
-// outside a buffer, so it is rejected here on the host.
+// bits partition [0, r_in) ([0, r_out)), every step's rest and kappa offsets
+// partition the tile positions it reads, its nu offsets avoid the rest
+// positions (so in-place writes never touch another rest index's entries),
+// and the store tables cover the final positions. Any violation would index
+// outside a buffer or race, so it is rejected here on the host.
 void validate_pass(const DevPass &P, const std::vector<int> &chunks) {
     auto bad = [](const char *what) { fail(TN_ERR_UNSUPPORTED, std::string("internal: pass ") + what); };
     if (P.r_in < 0 || P.r_in > 31 || P.r_out < 0 || P.r_out > 31) bad("rank");
-    if (P.t_in > MAX_TILE_BITS + 1 || P.t_out > MAX_TILE_BITS + 1) bad("tile bits");
     if (P.c_in > P.t_in || P.c_out > P.t_out) bad("chunk bits");
     if (P.n_steps < 1 || P.n_steps > MAX_PASS_STEPS) bad("step count");
     if (P.n_free > 32) bad("more than 32 free bits");
@@ -238,44 +278,60 @@ void validate_pass(const DevPass &P, const std::vector<int> &chunks) {
     };
     check_side(P.r_in, P.t_in, P.c_in, P.chunk_in_base, P.free_in);
     check_side(P.r_out, P.t_out, P.c_out, P.chunk_out_base, P.free_out);
-    int t = P.t_in;
+    // in-place steps: track which tile positions hold entries
+    if (P.tile_max < 1 || (P.tile_max & (P.tile_max - 1)) || P.tile_max > (1 << MAX_TILE_BITS))
+        bad("tile size");
+    if (P.t_in > MAX_TILE_BITS || P.t_out > MAX_TILE_BITS) bad("tile bits");
+    const uint32_t tile_mask = (uint32_t)P.tile_max - 1;
+    // undo the swizzle: tile_swizzle maps position bit q to a value whose top
+    // bit is q, and it is invertible on the tile
+    auto unswz = [&](int v) {
+        for (int q = 0; q < MAX_TILE_BITS; ++q)
+            if (tile_swizzle(1 << q) == v) return q;
+        return -1;
+    };
+    // single-bit images -> positions (distinct, inside the tile); every table
+    // entry must be the XOR of its single-bit entries
+    auto bits_of = [&](const int *tab, int nbits, int nentries, const char *what) {
+        uint32_t m = 0;
+        for (int b = 0; b < nbits; ++b) {
+            const int q = unswz(tab[1 << b]);
+            if (q < 0 || (m >> q) & 1u || !((tile_mask >> q) & 1u)) bad(what);
+            m |= 1u << q;
+        }
+        for (int v = 0; v < nentries; ++v) {
+            int o = 0;
+            for (int b = 0; b < nbits; ++b)
+                if ((v >> b) & 1) o ^= tab[1 << b];
+            if (tab[v] != o || (uint32_t)tab[v] > tile_mask) bad(what);
+        }
+        return m;
+    };
+    uint32_t occ = (P.t_in >= 32) ? 0u : ((1u << P.t_in) - 1);
+    if (occ & ~tile_mask) bad("input tile size");
     for (int i = 0; i < P.n_steps; ++i) {
         const DevStep &S = P.steps[i];
         if (S.k < 0 || S.n < 0 || S.k + S.n > MAX_STEP_K) bad("step k/n");
         if (S.branch >= 0 && S.k < 1) bad("fused step without contracted bits");
         if (S.branch < 0 && (S.k || S.n)) bad("copy step with k/n");
-        if (S.rest != t - S.k || S.rest > 12) bad("rest bits");
-        const int t2 = S.rest + S.n;
-        if ((1 << t) > P.tile_max || (1 << t2) > P.tile_max) bad("tile size");
-        uint64_t mi = 0, mo = 0;
-        // undo the swizzle: tile_swizzle is an involution on single bits' images
-        auto unswz = [](int v) {
-            for (int p = 0; p < 16; ++p)
-                if (tile_swizzle(1 << p) == v) return 1 << p;
-            return -1;
-        };
-        for (int b = 0; b < S.rest; ++b) {
-            int vi = unswz(b < 6 ? S.in_lo[1 << b] : S.in_hi[1 << (b - 6)]);
-            int vo = unswz(b < 6 ? S.out_lo[1 << b] : S.out_hi[1 << (b - 6)]);
-            if (vi <= 0 || (vi & (vi - 1)) || (mi & (uint64_t)vi)) bad("rest in offset");
-            if (vo <= 0 || (vo & (vo - 1)) || (mo & (uint64_t)vo)) bad("rest out offset");
-            mi |= (uint64_t)vi;
-            mo |= (uint64_t)vo;
-        }
-        for (int b = 0; b < S.k; ++b) {
-            int v = unswz(S.koff[1 << b]);
-            if (v <= 0 || (v & (v - 1)) || (mi & (uint64_t)v)) bad("kappa offset");
-            mi |= (uint64_t)v;
-        }
-        for (int b = 0; b < S.n; ++b) {
-            int v = unswz(S.noff[1 << b]);
-            if (v <= 0 || (v & (v - 1)) || (mo & (uint64_t)v)) bad("nu offset");
-            mo |= (uint64_t)v;
-        }
-        if (mi != (1ull << t) - 1 || mo != (1ull << t2) - 1) bad("tile partition");
-        t = t2;
+        if (S.rest != __builtin_popcount(occ) - S.k || S.rest > 12) bad("rest bits");
+        const int lo_bits = std::min(S.rest, 6), hi_bits = std::max(S.rest - 6, 0);
+        const uint32_t R = bits_of(S.lo, lo_bits, 1 << lo_bits, "rest offset") |
+                           bits_of(S.hi, hi_bits, 1 << hi_bits, "rest offset");
+        if (__builtin_popcount(R) != S.rest) bad("rest offset overlap");
+        const uint32_t Kp = bits_of(S.koff, S.k, 1 << S.k, "kappa offset");
+        const uint32_t Np = bits_of(S.noff, S.n, 1 << S.n, "nu offset");
+        if ((R & Kp) || (R | Kp) != occ) bad("step reads");
+        if (R & Np) bad("step writes");
+        occ = R | Np;
     }
-    if (t != P.t_out) bad("final tile bits");
+    if (__builtin_popcount(occ) != P.t_out) bad("final tile bits");
+    {
+        const int lo_bits = std::min(P.t_out, 6), hi_bits = std::max(P.t_out - 6, 0);
+        const uint32_t O = bits_of(P.st_lo, lo_bits, 1 << lo_bits, "store offset") |
+                           bits_of(P.st_hi, hi_bits, 1 << hi_bits, "store offset");
+        if (O != occ) bad("store positions");
+    }
     if (P.n_tiles != (1ll << P.n_free)) bad("tile count");
 }
 
