@@ -180,14 +180,16 @@ constexpr int MAX_TILE_BITS = 12;
 constexpr int MAX_BRANCH_SLICED = 24;
 constexpr int MAX_FREE = 40;
 
-// Shared-memory tiles are addressed through a bank swizzle: tile position p
-// lives at tile_swizzle(p) = p ^ (bits 4-7 of p) ^ rot2(bits 8-11 of p) in
-// the low four bits. The map is linear over GF(2), so offsets of disjoint bit
-// sets combine with XOR; it spreads power-of-two strides of 16 and 256
-// entries over all 16 eight-byte bank pairs.
+// Shared-memory tiles are addressed through a bank swizzle: tile position
+// bit 4+j also flips offset bit 1 + (j mod 3), i.e. tile_swizzle(p) = p ^
+// (s << 1) with s the XOR of the 3-bit fields of p >> 4. Offset bit 0 never
+// moves, so entry pairs (2i, 2i+1) stay adjacent and tiles move with 16-byte
+// copies; strides of 16 entries and more still land on distinct bank pairs.
+// The map is linear over GF(2), so offsets of disjoint bit sets combine with
+// XOR.
 inline int tile_swizzle(int p) {
-    const int a = (p >> 4) & 15, b = (p >> 8) & 15;
-    return p ^ a ^ (((b << 2) | (b >> 2)) & 15);
+    const int x = (p >> 4) & 255;
+    return p ^ (((x ^ (x >> 3) ^ (x >> 6)) & 7) << 1);
 }
 
 // All offsets are in complex elements; tile offsets are swizzled positions.
@@ -203,6 +205,9 @@ struct alignas(16) DevStep {
     int branch;                 // index into DevBranch table (-1: no step)
     int koff[16], noff[16];     // tile offsets of kappa / nu bits
     int lo[64], hi[64];         // rest index bits 0-5 / 6-11 -> tile offset
+    int pair;                   // 1: rest bit 0 is tile position 0 (offset 1),
+                                // so rest indices 2i, 2i+1 are adjacent entries
+    int pad_[3];
 };
 struct DevBranch {
     int64_t base;           // offset into the branch pool

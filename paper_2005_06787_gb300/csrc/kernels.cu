@@ -32,8 +32,8 @@ __device__ __forceinline__ int64_t branch_offset(const DevBranch &b, int p, int6
 // ---------------------------------------------------------------- fused pass
 // Tile bank swizzle (same map as tile_swizzle on the host).
 __device__ __forceinline__ int dev_swizzle(int p) {
-    const int a = (p >> 4) & 15, b = (p >> 8) & 15;
-    return p ^ a ^ (((b << 2) | (b >> 2)) & 15);
+    const int x = (p >> 4) & 255;
+    return p ^ (((x ^ (x >> 3) ^ (x >> 6)) & 7) << 1);
 }
 
 // One stem step on the tile, in place: for each rest index rho (one per
@@ -73,7 +73,54 @@ __device__ __forceinline__ void step_body(float2 *tile, const DevStep &S, const 
     }
 }
 
+// The same step with rest indices taken in adjacent pairs: rest-index bit 0
+// is tile position 0 (offset bit 0), so the entries of rest indices 2i and
+// 2i+1 sit side by side and move with one 16-byte access per kappa / nu.
+template <int K, int N>
+__device__ __forceinline__ void step_body_pair(float2 *tile, const DevStep &S,
+                                               const float2 *__restrict__ Bm, int nt) {
+    constexpr int NK = 1 << K, NN = 1 << N;
+    float2 bv[NK * NN];
+#pragma unroll
+    for (int i = 0; i < NK * NN; ++i) bv[i] = Bm[i];
+    int koff[NK], noff[NN];
+#pragma unroll
+    for (int kk = 0; kk < NK; ++kk) koff[kk] = S.koff[kk];
+#pragma unroll
+    for (int nn = 0; nn < NN; ++nn) noff[nn] = S.noff[nn];
+    const int npair = 1 << (S.rest - 1);
+    const int t_lo = S.lo[(2 * threadIdx.x) & 63];
+    for (int r2 = threadIdx.x; r2 < npair; r2 += nt) {
+        const int t = t_lo ^ S.hi[r2 >> 5];
+        float4 x[NK];
+#pragma unroll
+        for (int kk = 0; kk < NK; ++kk) x[kk] = *reinterpret_cast<const float4 *>(tile + (t ^ koff[kk]));
+#pragma unroll
+        for (int nn = 0; nn < NN; ++nn) {
+            float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int kk = 0; kk < NK; ++kk) {
+                const float2 b = bv[kk * NN + nn];
+                cfma(a0, make_float2(x[kk].x, x[kk].y), b);
+                cfma(a1, make_float2(x[kk].z, x[kk].w), b);
+            }
+            *reinterpret_cast<float4 *>(tile + (t ^ noff[nn])) = make_float4(a0.x, a0.y, a1.x, a1.y);
+        }
+    }
+}
+
 __device__ void run_step(float2 *tile, const DevStep &S, const float2 *Bm, int nt) {
+    if (S.pair) {
+        switch (S.k * 8 + S.n) {
+#define TN_CASE(K, N) \
+    case K * 8 + N: step_body_pair<K, N>(tile, S, Bm, nt); return;
+            TN_CASE(1, 0) TN_CASE(1, 1) TN_CASE(1, 2) TN_CASE(1, 3)
+            TN_CASE(2, 0) TN_CASE(2, 1) TN_CASE(2, 2)
+            TN_CASE(3, 0)
+#undef TN_CASE
+            default: break;
+        }
+    }
     switch (S.k * 8 + S.n) {
 #define TN_CASE(K, N) \
     case K * 8 + N: step_body<K, N>(tile, S, Bm, nt); break;
@@ -86,8 +133,12 @@ __device__ void run_step(float2 *tile, const DevStep &S, const float2 *Bm, int n
     }
 }
 
-// Asynchronous 8-byte global -> shared copy (Ampere-style cp.async; the
-// tile's bank swizzle permutes single entries, so copies are entry-sized).
+// Asynchronous global -> shared copies (cp.async): 16 bytes = one entry
+// pair (bypassing L1), or 8 bytes = one entry for rank-0 tensors.
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
 __device__ __forceinline__ void cp_async8(void *smem_dst, const void *gmem_src) {
     const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gmem_src) : "memory");
@@ -134,12 +185,15 @@ pass_kernel(const DevPass *__restrict__ gpass, const int *__restrict__ chunks,
     float2 *bm = tbuf + 2 * tile_max;
     for (int i = threadIdx.x; i < n_cin; i += PASS_THREADS) cin_tab[i] = chunks[P.chunk_in_base + i];
     for (int i = threadIdx.x; i < n_cout; i += PASS_THREADS) cout_tab[i] = chunks[P.chunk_out_base + i];
-    auto bm_off = [&](int t) {
+    // offsets of each step's branch matrix in bm
+    __shared__ int bm_off[MAX_PASS_STEPS];
+    if (threadIdx.x == 0) {
         int o = 0;
-        for (int u = 0; u < t; ++u)
-            if (P.steps[u].branch >= 0) o += 1 << (P.steps[u].k + P.steps[u].n);
-        return o;
-    };
+        for (int t = 0; t < P.n_steps; ++t) {
+            bm_off[t] = o;
+            if (P.steps[t].branch >= 0) o += 1 << (P.steps[t].k + P.steps[t].n);
+        }
+    }
     const int64_t n_units = (int64_t)ba.n_items * P.n_tiles;
     const int64_t base = ba.state->slice_base;
     const int64_t send = ba.state->slice_end;
@@ -152,16 +206,21 @@ pass_kernel(const DevPass *__restrict__ gpass, const int *__restrict__ chunks,
     const unsigned my_fin = lane < (unsigned)nfree ? (unsigned)P.free_in[lane] : 0u;
     const unsigned my_fout = lane < (unsigned)nfree ? (unsigned)P.free_out[lane] : 0u;
     const int st_lo = P.st_lo[threadIdx.x & 63];
+    const int st_lo2 = P.st_lo[(2 * threadIdx.x) & 63];
+    const bool st_pair = c_out >= 1 && P.st_lo[1] == 1;
     __syncthreads();
     // unit u -> (batch item, prefix, slice); invalid past the slice range
+    const int SB = ba.SB;
     auto unit_item = [&](int64_t u, int &item, int &p, int64_t &s) {
         item = (int)(u >> nfree);
-        const int pl = item / ba.SB;
+        const int pl = (SB == 1) ? item : item / SB;
         p = ba.p0 + pl;
-        s = base + (item - pl * ba.SB);
+        s = base + (item - pl * SB);
         return s < send;
     };
-    // issue the cp.async copies of unit u's input tile into buffer dstb
+    // issue the cp.async copies of unit u's input tile into buffer dstb:
+    // entry pairs (the low input bit is a chunk bit, so pairs are contiguous
+    // in HBM, and the swizzle keeps them adjacent in the tile)
     auto issue_load = [&](int64_t u, float2 *dstb) {
         int item, p;
         int64_t s;
@@ -171,8 +230,13 @@ pass_kernel(const DevPass *__restrict__ gpass, const int *__restrict__ chunks,
         const float2 *src = (P.in_branch >= 0) ? pool + branch_offset(branches[P.in_branch], p, s)
                                                : in + (int64_t)item * P.in_item_stride;
         src += ib;
-        for (int idx = threadIdx.x; idx < tin_n; idx += PASS_THREADS)
-            cp_async8(dstb + dev_swizzle(idx), src + cin_tab[idx >> c_in] + (idx & cin_mask));
+        if (c_in >= 1) {
+            for (int idx = 2 * threadIdx.x; idx < tin_n; idx += 2 * PASS_THREADS)
+                cp_async16(dstb + dev_swizzle(idx), src + cin_tab[idx >> c_in] + (idx & cin_mask));
+        } else {
+            for (int idx = threadIdx.x; idx < tin_n; idx += PASS_THREADS)
+                cp_async8(dstb + dev_swizzle(idx), src + cin_tab[idx >> c_in] + (idx & cin_mask));
+        }
     };
     int last_item = -1;
     int buf = 0;
@@ -191,7 +255,7 @@ pass_kernel(const DevPass *__restrict__ gpass, const int *__restrict__ chunks,
                 if (br < 0) continue;
                 const float2 *bsrc = pool + branch_offset(branches[br], p, s);
                 const int cnt = 1 << (P.steps[t].k + P.steps[t].n);
-                const int bo = bm_off(t);
+                const int bo = bm_off[t];
                 for (int i = threadIdx.x; i < cnt; i += PASS_THREADS) bm[bo + i] = bsrc[i];
             }
             last_item = item;
@@ -201,14 +265,21 @@ pass_kernel(const DevPass *__restrict__ gpass, const int *__restrict__ chunks,
             float2 *tile = tbuf + buf * tile_max;
             for (int t = 0; t < P.n_steps; ++t) {
                 if (P.steps[t].branch < 0) continue;
-                run_step(tile, P.steps[t], bm + bm_off(t), PASS_THREADS);
+                run_step(tile, P.steps[t], bm + bm_off[t], PASS_THREADS);
                 __syncthreads();
             }
             const unsigned tl = (unsigned)(u & (P.n_tiles - 1));
             const unsigned ob = __reduce_or_sync(0xffffffffu, ((tl >> lane) & 1u) ? my_fout : 0u);
             float2 *dst = out + (int64_t)item * P.out_item_stride + ob;
-            for (int idx = threadIdx.x; idx < tout_n; idx += PASS_THREADS)
-                dst[cout_tab[idx >> c_out] + (idx & cout_mask)] = tile[st_lo ^ P.st_hi[idx >> 6]];
+            if (st_pair) {
+                // output bit 0 is tile position 0: entry pairs move as 16 bytes
+                for (int idx = 2 * threadIdx.x; idx < tout_n; idx += 2 * PASS_THREADS)
+                    *reinterpret_cast<float4 *>(dst + cout_tab[idx >> c_out] + (idx & cout_mask)) =
+                        *reinterpret_cast<const float4 *>(tile + (st_lo2 ^ P.st_hi[idx >> 6]));
+            } else {
+                for (int idx = threadIdx.x; idx < tout_n; idx += PASS_THREADS)
+                    dst[cout_tab[idx >> c_out] + (idx & cout_mask)] = tile[st_lo ^ P.st_hi[idx >> 6]];
+            }
         }
         __syncthreads();
     }

@@ -62,25 +62,48 @@ std::vector<int> sort_by_next_use(std::vector<int> edges, const std::vector<Step
 // tile position q lands on.
 int bank_vec(int q) { return tile_swizzle(1 << q) & 15; }
 
-// Order a step's rest edges into rest-index bits. Rest-index bits 0-3 vary
-// across the 16 lanes of a half-warp; they get edges whose bank vectors are
-// independent over GF(2) where the tile allows, so every half-warp's 8-byte
-// accesses fall on 16 distinct bank pairs. The others follow by position.
-std::vector<int> order_rest(std::vector<int> rest, const std::map<int, int> &pos) {
+// Steps whose rest indices a thread handles in adjacent pairs (16-byte
+// shared-memory accesses) when tile position 0 is a rest bit; the others keep
+// a register footprint the pass kernel can afford only one rest index at a
+// time.
+bool pair_shape(int k, int n) { return (k <= 2 && k + n <= 4) || (k == 3 && n == 0); }
+
+// GF(2) span helper over 4-bit bank vectors: adds v when independent.
+bool take_independent(uint32_t &span, int v) {
+    if (v == 0 || ((span >> v) & 1u)) return false;
+    uint32_t add = 0;
+    for (int x = 0; x < 16; ++x)
+        if ((span >> x) & 1u) add |= 1u << (x ^ v);
+    span |= add;
+    return true;
+}
+
+// Order a step's rest edges into rest-index bits. Plain steps: rest-index
+// bits 0-3 vary across the 16 lanes of a half-warp and get edges whose bank
+// vectors are independent over GF(2) where the tile allows, so every
+// half-warp's 8-byte accesses fall on 16 distinct bank pairs. Paired steps:
+// bit 0 is the position-0 edge (the pair inside a thread), and bits 1-3 vary
+// across the 8 lanes of a quarter-warp, whose 16-byte accesses are
+// conflict-free when those edges move distinct combinations of offset bits
+// 1-3. The others follow by position.
+std::vector<int> order_rest(std::vector<int> rest, const std::map<int, int> &pos, bool pair) {
     std::sort(rest.begin(), rest.end(), [&](int a, int b) { return pos.at(a) < pos.at(b); });
     std::vector<int> lanes, others;
     uint32_t span = 1;  // bit v set: vector v is in the span of the chosen vectors
-    for (int e : rest) {
+    size_t start = 0;
+    if (pair) {
+        lanes.push_back(rest[0]);  // position 0
+        start = 1;
+        span |= 1u << 1;           // offset bit 0 is inside the pair
+    }
+    const size_t want = 4;
+    for (size_t i = start; i < rest.size(); ++i) {
+        const int e = rest[i];
         const int v = bank_vec(pos.at(e));
-        if ((int)lanes.size() < 4 && v != 0 && !((span >> v) & 1u)) {
+        if (lanes.size() < want && take_independent(span, v))
             lanes.push_back(e);
-            uint32_t add = 0;
-            for (int x = 0; x < 16; ++x)
-                if ((span >> x) & 1u) add |= 1u << (x ^ v);
-            span |= add;
-        } else {
+        else
             others.push_back(e);
-        }
     }
     lanes.insert(lanes.end(), others.begin(), others.end());
     return lanes;
@@ -89,7 +112,8 @@ std::vector<int> order_rest(std::vector<int> rest, const std::map<int, int> &pos
 // Tables of one in-place step: kappa offsets at the positions before the
 // step, nu offsets at the positions after it, rest offsets (unchanged).
 void fill_step(DevStep &st, const std::vector<int> &rest, const std::vector<int> &kpos,
-               const std::vector<int> &npos, const std::map<int, int> &pos) {
+               const std::vector<int> &npos, const std::map<int, int> &pos, bool pair) {
+    st.pair = pair ? 1 : 0;
     st.k = (int)kpos.size();
     st.n = (int)npos.size();
     st.rest = (int)rest.size();
@@ -151,8 +175,8 @@ DevPass build_pass(const std::vector<int> &Lin, const std::vector<int> &Lout, in
     };
     if (group.empty()) {
         P.n_steps = 1;
-        std::vector<int> rest = order_rest(lam_in, pos);
-        fill_step(P.steps[0], rest, {}, {}, pos);
+        std::vector<int> rest = order_rest(lam_in, pos, false);
+        fill_step(P.steps[0], rest, {}, {}, pos, false);
         P.steps[0].branch = -1;
     } else {
         P.n_steps = (int)group.size();
@@ -167,7 +191,13 @@ DevPass build_pass(const std::vector<int> &Lin, const std::vector<int> &Lout, in
             std::vector<int> rest;
             for (auto &kv : pos)
                 if (std::find(S.K.begin(), S.K.end(), kv.first) == S.K.end()) rest.push_back(kv.first);
-            rest = order_rest(rest, pos);
+            bool pair = pair_shape((int)S.K.size(), (int)S.N.size());
+            if (pair) {
+                pair = false;
+                for (int e : rest)
+                    if (pos.at(e) == 0) pair = true;
+            }
+            rest = order_rest(rest, pos, pair);
             for (int e : S.K) pos.erase(e);
             std::vector<int> free_pos = kpos;
             const uint32_t occ = used();
@@ -176,7 +206,7 @@ DevPass build_pass(const std::vector<int> &Lin, const std::vector<int> &Lout, in
                     free_pos.push_back(q);
             std::vector<int> npos(free_pos.begin(), free_pos.begin() + (long)S.N.size());
             for (size_t b = 0; b < S.N.size(); ++b) pos[S.N[b]] = npos[b];
-            fill_step(P.steps[t], rest, kpos, npos, pos);
+            fill_step(P.steps[t], rest, kpos, npos, pos, pair);
             P.steps[t].branch = branch_of_step[(size_t)group[t]];
             max_t = std::max(max_t, (int)pos.size());
         }
@@ -322,6 +352,7 @@ void validate_pass(const DevPass &P, const std::vector<int> &chunks) {
         const uint32_t Kp = bits_of(S.koff, S.k, 1 << S.k, "kappa offset");
         const uint32_t Np = bits_of(S.noff, S.n, 1 << S.n, "nu offset");
         if ((R & Kp) || (R | Kp) != occ) bad("step reads");
+        if (S.pair && (S.rest < 1 || S.lo[1] != 1 || !pair_shape(S.k, S.n))) bad("paired step");
         if (R & Np) bad("step writes");
         occ = R | Np;
     }
