@@ -45,7 +45,7 @@ METRIC = "stem TFLOP/s and slices/s at 53q/14-cycle, chosen vs plain FP32 at <=1
 def plan_options(name: str) -> dict:
     """Planner options of each workload (shared by the bench and its tests)."""
     cfg = CONFIGS[name]
-    o = dict(cw_limit=cfg.get("cw_limit") or 30, restarts=8, local_opt_iters=4, seed=0x5EED)
+    o = dict(cw_limit=cfg.get("cw_limit") or 30, restarts=3, local_opt_iters=4, seed=0x5EED)
     if cfg.get("n_sliced"):
         o["min_sliced"] = cfg["n_sliced"]
     return o
@@ -240,7 +240,7 @@ def run_learned(args):
     for wl in ("grid5x6_m14", "diag53_m12", "diag53_m14"):
         c, oq, cb = workload_inputs(wl)
         net = P.tn_build_network(c, oq, cb)
-        for plan in learned.plan_variants(net, plan_options(wl), tiles=(11, 12), steps=(4, 8),
+        for plan in learned.plan_variants(net, dict(plan_options(wl), anneal_iters=-1), tiles=(11, 12), steps=(4, 8),
                                           merges=(0, 3)):
             P.tn_plan_prepare(plan, stream=stream)
             precs = ("fp32", "tf32x3") if P.tn_plan_info(plan)["n_gemm_steps"] else ("fp32",)
@@ -256,7 +256,7 @@ def run_learned(args):
     name = "diag53_m20"
     c, oq, cb = workload_inputs(name)
     net = P.tn_build_network(c, oq, cb)
-    base = dict(plan_options(name), max_sliced=60, restarts=4)
+    base = dict(plan_options(name), max_sliced=60, restarts=1, anneal_iters=100000)
     out = torch.zeros(2 * (1 << len(oq)), dtype=torch.float64, device="cuda")
     res = {}
     for label, m in (("mlp", mlp), ("flop", None)):

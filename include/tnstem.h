@@ -95,6 +95,9 @@ typedef struct {
     int32_t merge_group;      /* Supp. A.3 branch merging: merge runs of this many
                                  consecutive stem branches into one (0/1 = off) */
     int32_t merge_rank_cap;   /* largest rank of a merged branch (0 = 10) */
+    int32_t anneal_iters;     /* simulated-annealing moves on the stem order per
+                                 restart (0 = auto: 600 per branch cluster, at
+                                 most 200000; < 0 = none) */
     uint64_t seed;
 } tn_plan_opts;
 

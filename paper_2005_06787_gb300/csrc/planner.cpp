@@ -248,12 +248,15 @@ static bool local_opt(const std::vector<Bits> &B, int seed, std::vector<int> &or
             return scheme_score(e, n_sliced, limit);
         };
         double best = score_of(tc0, mx0);
+        // never widen the stem beyond max(limit, its current width)
+        const int cap = std::max(limit, std::max(out_max, mx0));
         std::vector<int> perm(win), bestp(win);
         std::sort(perm.begin(), perm.end());
         do {
             double tc;
             int mx;
             eval_win(perm, tc, mx);
+            if (std::max(out_max, mx) > cap) continue;
             double s = score_of(tc, mx);
             if (s < best - 1e-12) {
                 best = s;
@@ -275,12 +278,194 @@ static void local_opt_sweeps(const std::vector<Bits> &B, int seed, std::vector<i
         if (!local_opt(B, seed, order, sliced, limit, 4, n_sliced)) break;
 }
 
+// Supp. A.2 "Local optimization", widened: simulated annealing over the
+// stem order. A move takes one branch out of the order and puts it back up
+// to `window` places away; only the stem tensors between the two places
+// change, so a move is scored by recomputing that stretch. Score: log2 of
+// the stem cost plus one unit per bit the widest stem tensor exceeds the
+// limit (each such bit costs about one more sliced edge). Metropolis
+// acceptance at a temperature falling geometrically from t0 to t1.
+static void anneal_order(const std::vector<Bits> &B, int seed, std::vector<int> &order,
+                         const Bits &sliced, int limit, long iters, std::mt19937_64 &rng,
+                         double t0 = 1.0, double t1 = 0.02, int window = 48, int cap_rank = 1 << 30) {
+    const int L = (int)order.size();
+    if (L < 3 || iters <= 0) return;
+    std::vector<Bits> Bs(B.size());
+    for (size_t i = 0; i < B.size(); ++i) Bs[i] = B[i].andnot(sliced);
+    std::vector<Bits> pre((size_t)L + 1);
+    std::vector<double> cost((size_t)L);  // 2^|E_u| of each stem step
+    std::vector<int> rank((size_t)L + 1);
+    pre[0] = Bs[(size_t)seed];
+    rank[0] = pre[0].count();
+    for (int i = 0; i < L; ++i) {
+        const Bits &b = Bs[(size_t)order[(size_t)i]];
+        cost[(size_t)i] = std::exp2((double)count_or(pre[(size_t)i], b));
+        pre[(size_t)i + 1] = pre[(size_t)i] ^ b;
+        rank[(size_t)i + 1] = pre[(size_t)i + 1].count();
+    }
+    double total = 0;
+    for (double c : cost) total += c;
+    auto max_rank = [&](const std::vector<int> &r) { return *std::max_element(r.begin(), r.end()); };
+    auto score = [&](double tot, int mr) { return std::log2(tot) + std::max(0, mr - limit); };
+    double cur = score(total, max_rank(rank));
+    std::vector<int> best_order = order;
+    double best = cur;
+    std::uniform_real_distribution<double> U(0.0, 1.0);
+    std::uniform_int_distribution<int> pos(0, L - 1);
+    std::uniform_int_distribution<int> off(-window, window);
+    std::vector<Bits> npre;
+    std::vector<double> ncost;
+    std::vector<int> nrank(rank);
+    std::vector<int> seg;
+    for (long it = 0; it < iters; ++it) {
+        const double T = t0 * std::pow(t1 / t0, (double)it / (double)iters);
+        const int i = pos(rng);
+        int j = i + off(rng);
+        if (j < 0 || j >= L || j == i) continue;
+        const int lo = std::min(i, j), hi = std::max(i, j);
+        // new order of positions lo..hi
+        seg.assign(order.begin() + lo, order.begin() + hi + 1);
+        if (i < j)
+            std::rotate(seg.begin(), seg.begin() + 1, seg.end());
+        else
+            std::rotate(seg.begin(), seg.end() - 1, seg.end());
+        npre.resize(seg.size() + 1);
+        ncost.resize(seg.size());
+        npre[0] = pre[(size_t)lo];
+        double old_part = 0, new_part = 0;
+        for (size_t t = 0; t < seg.size(); ++t) {
+            const Bits &b = Bs[(size_t)seg[t]];
+            ncost[t] = std::exp2((double)count_or(npre[t], b));
+            npre[t + 1] = npre[t] ^ b;
+            new_part += ncost[t];
+            old_part += cost[(size_t)lo + t];
+        }
+        for (size_t t = 1; t < seg.size(); ++t) nrank[(size_t)lo + t] = npre[t].count();
+        const double ntotal = total - old_part + new_part;
+        const int nmax = max_rank(nrank);
+        const double nscore = score(ntotal, nmax);
+        const double d = nscore - cur;
+        if (nmax <= cap_rank && (d <= 0 || U(rng) < std::exp(-d / T))) {
+            std::copy(seg.begin(), seg.end(), order.begin() + lo);
+            for (size_t t = 0; t < seg.size(); ++t) {
+                cost[(size_t)lo + t] = ncost[t];
+                pre[(size_t)lo + t + 1] = npre[t + 1];
+            }
+            rank = nrank;
+            total = ntotal;
+            cur = nscore;
+            if (cur < best - 1e-12) {
+                best = cur;
+                best_order = order;
+            }
+        } else {
+            for (size_t t = 1; t < seg.size(); ++t) nrank[(size_t)lo + t] = rank[(size_t)lo + t];
+        }
+    }
+    order = best_order;
+}
+
+// Joint refinement of the stem order and the sliced set once the width is
+// within the limit: besides the order moves of anneal_order, a move swaps
+// one sliced edge for an unsliced edge of a widest stem tensor, or drops a
+// sliced edge (never below min_sliced). The score is the total cost over all
+// slices, log2 stem cost + |sliced|, and the width limit is hard, so the
+// search keeps slices on edges that live through the expensive part of the
+// stem (those slice almost for free, as the paper observes for its stems).
+static void anneal_sliced(const Network &net, const std::vector<Bits> &B, int seed,
+                          std::vector<int> &order, Bits &sliced, std::vector<int> &sliced_list,
+                          int limit, int min_sliced, long iters, std::mt19937_64 &rng) {
+    const int L = (int)order.size();
+    if (L < 3 || iters <= 0 || sliced_list.empty()) return;
+    Bits open(net.n_edges());
+    for (int e : net.open_edges) open.set(e);
+    auto evaluate = [&](const std::vector<int> &ord, const Bits &sl, int nsl, std::vector<Bits> *wide) {
+        Bits S = B[(size_t)seed].andnot(sl);
+        double tot = 0;
+        int mr = S.count();
+        std::vector<Bits> tens;
+        if (wide) tens.push_back(S);
+        for (int c : ord) {
+            const Bits b = B[(size_t)c].andnot(sl);
+            tot += std::exp2((double)count_or(S, b));
+            S ^= b;
+            mr = std::max(mr, S.count());
+            if (wide) tens.push_back(S);
+        }
+        if (wide) {
+            wide->clear();
+            for (auto &t : tens)
+                if (t.count() >= mr) wide->push_back(t);
+        }
+        if (mr > limit) return (double)INFINITY;  // the width limit is hard once met
+        return std::log2(tot) + nsl;
+    };
+    std::vector<Bits> wide;
+    double cur = evaluate(order, sliced, (int)sliced_list.size(), &wide);
+    double best = cur;
+    std::vector<int> best_order = order, best_list = sliced_list;
+    Bits best_sliced = sliced;
+    std::uniform_real_distribution<double> U(0.0, 1.0);
+    std::uniform_int_distribution<int> pos(0, L - 1), off(-32, 32);
+    const double t0 = 0.3, t1 = 0.005;
+    for (long it = 0; it < iters; ++it) {
+        const double T = t0 * std::pow(t1 / t0, (double)it / (double)iters);
+        std::vector<int> ord2 = order;
+        Bits sl2 = sliced;
+        std::vector<int> list2 = sliced_list;
+        const double r = U(rng);
+        if (r < 0.7) {
+            const int i = pos(rng), j = i + off(rng);
+            if (j < 0 || j >= L || j == i) continue;
+            const int v = ord2[(size_t)i];
+            ord2.erase(ord2.begin() + i);
+            ord2.insert(ord2.begin() + j, v);
+        } else if (r < 0.95 || list2.size() < 2 || (int)list2.size() <= min_sliced) {
+            // swap a sliced edge for an unsliced edge of a widest tensor
+            std::vector<int> cand;
+            for (auto &t : wide)
+                for (int e : t.list())
+                    if (!open.test(e)) cand.push_back(e);
+            if (cand.empty()) continue;
+            const int e_new = cand[(size_t)(U(rng) * (double)cand.size()) % cand.size()];
+            const size_t k = (size_t)(U(rng) * (double)list2.size()) % list2.size();
+            sl2.reset(list2[k]);
+            sl2.set(e_new);
+            list2[k] = e_new;
+        } else {
+            const size_t k = (size_t)(U(rng) * (double)list2.size()) % list2.size();
+            sl2.reset(list2[k]);
+            list2.erase(list2.begin() + (long)k);
+        }
+        std::vector<Bits> wide2;
+        const double sc = evaluate(ord2, sl2, (int)list2.size(), &wide2);
+        const double d = sc - cur;
+        if (d <= 0 || U(rng) < std::exp(-d / T)) {
+            order.swap(ord2);
+            sliced = sl2;
+            sliced_list.swap(list2);
+            wide.swap(wide2);
+            cur = sc;
+            if (cur < best - 1e-12) {
+                best = cur;
+                best_order = order;
+                best_sliced = sliced;
+                best_list = sliced_list;
+            }
+        }
+    }
+    order = best_order;
+    sliced = best_sliced;
+    sliced_list = best_list;
+}
+
 // Supp. A.2 "Dynamic slicing": slice, one edge at a time, the edge of the
 // widest stem tensors whose slicing raises the total cost least (ties: the
 // lowest edge id), with local optimisation in between.
 static bool dynamic_slice(const Network &net, const std::vector<Bits> &B, int seed,
                           std::vector<int> &order, Bits &sliced, std::vector<int> &sliced_list,
-                          int limit, int min_sliced, int max_sliced, int lo_iters) {
+                          int limit, int min_sliced, int max_sliced, int lo_iters, long anneal,
+                          std::mt19937_64 &rng) {
     Bits open(net.n_edges());
     for (int e : net.open_edges) open.set(e);
     while (true) {
@@ -320,6 +505,9 @@ static bool dynamic_slice(const Network &net, const std::vector<Bits> &B, int se
         }
         sliced.set(best_e);
         sliced_list.push_back(best_e);
+        // restructure without widening the stem beyond its current width
+        const int cap = eval_stem(B, seed, order, sliced).max_rank;
+        anneal_order(B, seed, order, sliced, limit, anneal, rng, 0.3, 0.01, 48, cap);
         local_opt_sweeps(B, seed, order, sliced, limit, lo_iters, (int)sliced_list.size());
     }
 }
@@ -354,6 +542,8 @@ Scheme plan_scheme(const Network &net, const tn_plan_opts &o) {
     const int lo_iters = o.local_opt_iters > 0 ? o.local_opt_iters : 4;
     const int cap = o.branch_rank > 0 ? o.branch_rank : 4;
     const int max_sl = o.max_sliced > 0 ? o.max_sliced : 40;
+    // annealing moves per restart: explicit, off (< 0), or by default 600 per
+    // branch cluster (at most 200000)
     std::mt19937_64 rng(o.seed ? o.seed : 0x5eedull);
     Scheme best;
     double best_score = INFINITY;
@@ -361,6 +551,9 @@ Scheme plan_scheme(const Network &net, const tn_plan_opts &o) {
     std::vector<Bits> B;
     for (auto &c : clusters) B.push_back(c.out);
     const int C = (int)clusters.size();
+    const long anneal = o.anneal_iters > 0   ? (long)o.anneal_iters
+                        : o.anneal_iters < 0 ? 0L
+                                             : std::min(200000L, 600L * (long)C);
     if (C == 1) {
         Scheme s;
         s.clusters = clusters;
@@ -377,12 +570,16 @@ Scheme plan_scheme(const Network &net, const tn_plan_opts &o) {
         std::vector<int> order = grow_stem(B, seed, rng, noise);
         Bits sliced(net.n_edges());
         std::vector<int> sl;
+        anneal_order(B, seed, order, sliced, limit, anneal, rng);
         local_opt_sweeps(B, seed, order, sliced, limit, lo_iters, 0);
         bool ok = dynamic_slice(net, B, seed, order, sliced, sl, limit, o.min_sliced, max_sl,
-                                lo_iters);
+                                lo_iters, anneal / 10, rng);
         if (!ok) continue;
+        anneal_order(B, seed, order, sliced, limit, anneal / 2, rng, 0.3, 0.01, 48, limit);
+        anneal_sliced(net, B, seed, order, sliced, sl, limit, o.min_sliced, anneal / 4, rng);
         local_opt_sweeps(B, seed, order, sliced, limit, lo_iters, (int)sl.size());
         StemEval ev = eval_stem(B, seed, order, sliced);
+        if (ev.max_rank > limit) continue;
         double sc = scheme_score(ev, (int)sl.size(), limit);
         if (sc < best_score) {
             best_score = sc;
