@@ -522,6 +522,11 @@ def main():
             "e2e": {"value": e2e_sps * flops_per_slice / 1e12, "unit": "TFLOP/s",
                     "slices_per_s": e2e_sps, "h2d_bytes_per_step": 16,
                     "d2h_bytes_per_step": 16 * nb},
+            # the whole 64-amplitude batch: every slice of the plan at this rate
+            "job": {"slices": 2 ** info["n_sliced"], "log2_tc_total": info["log2_tc"],
+                    "seconds": 2 ** info["n_sliced"] / slices_per_s,
+                    "context": "paper Table 1, Sycamore-53 m=14 on one V100: 243.71 s, 2^10 "
+                               "slices, tc 7.16e13 (another circuit and machine)"},
             "roofline": roofline,
             "launch_breakdown": by_kind,
             "plain_breakdown": plain_kind,
