@@ -22,6 +22,10 @@ Contents and the passages they follow:
 * ``tree_cost``: tc and cw of a contraction scheme (Supp. A.1: per step
   2^|E_AB| and |E*_AB|; tc sums, cw maxes; slicing multiplies tc by 2^|E_s|).
 * ``linear_xeb``: 2^n <p> - 1 (Sec. 2).
+* ``frugal_sample``: frugal rejection sampling over amplitude batches (Sec.
+  2, after the method the paper cites as MFI+18): candidate x is accepted
+  with probability min(1, 2^n p(x) / M); a batch yields its first accepted
+  candidate in a random visiting order.
 
 Leaf numbering (shared convention, each side implements it itself): leaves
 0..n-1 are |0> on qubits 0..n-1; then for each cycle t < m the single-qubit
@@ -368,3 +372,34 @@ def tree_cost(edges: List[List[Edge]], open_edges: Sequence[Edge],
 def linear_xeb(probs: np.ndarray, n_qubits: int) -> float:
     """Sec. 2: 2^n <p_I(x)> - 1 over the sampled bitstrings' ideal p."""
     return float((2.0 ** n_qubits) * np.mean(probs) - 1.0)
+
+
+def frugal_sample(amps: np.ndarray, n_qubits: int, M: float, u: np.ndarray,
+                  key: np.ndarray) -> Tuple[np.ndarray, np.ndarray]:
+    """Frugal rejection sampling (Sec. 2): for batch b and candidate j,
+    p = |amps[b, j]|^2 and the candidate is accepted when
+    u[b, j] < 2^n p / M (the acceptance probability min(1, 2^n p / M) for u
+    uniform in [0, 1)). The batch's sample is the accepted candidate with the
+    smallest key[b, j] (keys uniform: a random visiting order, first accepted
+    wins; equal keys go to the lower j), or -1 when none is accepted.
+
+    The acceptance test is evaluated in FP64 as ((re*re + im*im) * 2^n) / M
+    with each operation rounded separately. Returns (index [B], accepted
+    count [B]), both int64."""
+    a = np.asarray(amps, dtype=np.complex128)
+    B, K = a.shape
+    re, im = a.real.copy(), a.imag.copy()
+    p = re * re + im * im
+    thr = (p * (2.0 ** n_qubits)) / float(M)
+    acc = np.asarray(u, dtype=np.float64) < thr
+    idx = np.full(B, -1, dtype=np.int64)
+    cnt = acc.sum(axis=1).astype(np.int64)
+    keys = np.asarray(key, dtype=np.float64)
+    for b in range(B):
+        best = None
+        for j in range(K):
+            if acc[b, j] and (best is None or keys[b, j] < keys[b, best]):
+                best = j
+        if best is not None:
+            idx[b] = best
+    return idx, cnt

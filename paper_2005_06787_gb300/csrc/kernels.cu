@@ -54,8 +54,10 @@ __device__ __forceinline__ void step_body(float2 *tile, const DevStep &S, const 
     int koff[NK], noff[NN];
 #pragma unroll
     for (int kk = 0; kk < NK; ++kk) koff[kk] = S.koff[kk];
+    // k == n: the nu bits took the kappa positions in order, so results go
+    // where their inputs were (the host checks noff == koff for such steps)
 #pragma unroll
-    for (int nn = 0; nn < NN; ++nn) noff[nn] = S.noff[nn];
+    for (int nn = 0; nn < NN; ++nn) noff[nn] = (K == N) ? koff[nn % NK] : S.noff[nn];
     const int nrest = 1 << S.rest;
     const int t_lo = S.lo[threadIdx.x & 63];
     for (int r = threadIdx.x; r < nrest; r += nt) {
@@ -86,8 +88,10 @@ __device__ __forceinline__ void step_body_pair(float2 *tile, const DevStep &S,
     int koff[NK], noff[NN];
 #pragma unroll
     for (int kk = 0; kk < NK; ++kk) koff[kk] = S.koff[kk];
+    // k == n: the nu bits took the kappa positions in order, so results go
+    // where their inputs were (the host checks noff == koff for such steps)
 #pragma unroll
-    for (int nn = 0; nn < NN; ++nn) noff[nn] = S.noff[nn];
+    for (int nn = 0; nn < NN; ++nn) noff[nn] = (K == N) ? koff[nn % NK] : S.noff[nn];
     const int npair = 1 << (S.rest - 1);
     const int t_lo = S.lo[(2 * threadIdx.x) & 63];
     for (int r2 = threadIdx.x; r2 < npair; r2 += nt) {

@@ -353,6 +353,9 @@ void validate_pass(const DevPass &P, const std::vector<int> &chunks) {
         const uint32_t Np = bits_of(S.noff, S.n, 1 << S.n, "nu offset");
         if ((R & Kp) || (R | Kp) != occ) bad("step reads");
         if (S.pair && (S.rest < 1 || S.lo[1] != 1 || !pair_shape(S.k, S.n))) bad("paired step");
+        if (S.k == S.n)  // the kernel writes k == n results at the kappa offsets
+            for (int v = 0; v < (1 << S.k); ++v)
+                if (S.noff[v] != S.koff[v]) bad("k == n step not in place");
         if (R & Np) bad("step writes");
         occ = R | Np;
     }

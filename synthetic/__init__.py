@@ -14,6 +14,7 @@ from .circuits import (  # noqa: F401
     diagonal53_layout,
     random_circuit,
     random_bits,
+    random_uniform,
     config_circuit,
     CONFIGS,
 )

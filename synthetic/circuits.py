@@ -178,6 +178,15 @@ def random_bits(n_bits: int, seed: int) -> np.ndarray:
     return np.asarray([rng.below(2) for _ in range(n_bits)], dtype=np.uint8)
 
 
+def random_uniform(shape: Sequence[int], seed: int) -> np.ndarray:
+    """Uniform doubles in [0, 1): the top 53 bits of SplitMix64 draws, in
+    row-major order (random numbers a method consumes are inputs)."""
+    rng = SplitMix64(seed)
+    n = int(np.prod(shape))
+    return (np.asarray([rng.next() >> 11 for _ in range(n)], dtype=np.float64) *
+            (1.0 / 9007199254740992.0)).reshape(shape)
+
+
 def random_complex(shape: Sequence[int], seed: int = 7, dtype=np.complex128) -> np.ndarray:
     """N(0,1) complex test tensor (real and imaginary parts independent)."""
     rng = np.random.default_rng(seed)

@@ -20,7 +20,7 @@ import numpy as np
 import pytest
 
 import oracle
-from synthetic.circuits import Circuit, grid_layout, random_circuit, random_bits
+from synthetic.circuits import Circuit, grid_layout, random_circuit, random_bits, random_uniform
 
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -343,3 +343,70 @@ def test_planted_wrong_projector_value_fails_sv_pin():
     flipped[3] ^= 1
     sv = oracle.sv_amplitudes(c, oq, flipped)
     assert np.abs(oracle.contract(net).reshape(-1) - sv).max() > 1e-6
+
+
+# ------------------------------------------------------- frugal sampling (Sec. 2)
+# Frugal rejection sampling accepts candidate x with probability
+# min(1, 2^n p(x) / M). Pins: the mean accepted count equals the sum of those
+# probabilities; with rare acceptance the selected bitstrings follow p; on a
+# deep (Porter-Thomas) circuit the samples' linear XEB is about 1 while
+# uniform bitstrings give about 0; and the degenerate thresholds.
+
+def _deep_probs(rows, cols, m, seed):
+    c = random_circuit(grid_layout(rows, cols), m, seed)
+    psi = oracle.statevector(c)
+    return c, psi, np.abs(psi) ** 2
+
+
+def test_frugal_accept_count_matches_closed_form():
+    c, psi, p = _deep_probs(2, 5, 12, 31)
+    n, K = 10, 1024
+    M, R = 10.0, 300
+    u = random_uniform((R, K), 9001)
+    key = random_uniform((R, K), 9002)
+    amps = np.broadcast_to(psi, (R, K))
+    _, cnt = oracle.frugal_sample(amps, n, M, u, key)
+    expect = np.minimum(1.0, (2.0 ** n) * p / M).sum()
+    var = (np.minimum(1.0, (2.0 ** n) * p / M) * (1 - np.minimum(1.0, (2.0 ** n) * p / M))).sum()
+    assert abs(cnt.mean() - expect) < 5 * math.sqrt(var / R)
+    # degenerate thresholds: M huge accepts nothing, M tiny accepts every p > 0
+    idx0, cnt0 = oracle.frugal_sample(amps[:3], n, 1e300, u[:3], key[:3])
+    assert (idx0 == -1).all() and (cnt0 == 0).all()
+    _, cnt1 = oracle.frugal_sample(amps[:3], n, 1e-300, u[:3], key[:3])
+    assert (cnt1 == (p > 0).sum()).all()
+
+
+def test_frugal_samples_follow_p():
+    c, psi, p = _deep_probs(2, 3, 10, 32)
+    n, K, B = 6, 64, 20000
+    u = random_uniform((B, K), 9003)
+    key = random_uniform((B, K), 9004)
+    idx, _ = oracle.frugal_sample(np.broadcast_to(psi, (B, K)), n, 40.0, u, key)
+    got = idx[idx >= 0]
+    assert len(got) > 0.6 * B
+    freq = np.bincount(got, minlength=K) / len(got)
+    tv = 0.5 * np.abs(freq - p).sum()
+    assert tv < 0.06, tv
+    # a sampler that weighted by |amplitude| instead of |amplitude|^2 is far off
+    q = np.abs(psi) / np.abs(psi).sum()
+    assert 0.5 * np.abs(q - p).sum() > 0.1
+
+
+def test_frugal_samples_xeb_near_one_on_deep_circuit():
+    c = random_circuit(grid_layout(3, 4), 14, 33)
+    psi = oracle.statevector(c)
+    oq = [0, 1, 2, 3, 4, 5]
+    n, B = 12, 600
+    prefixes = [list(random_bits(6, 7000 + b)) for b in range(B)]
+    amps = np.stack([oracle.sv_amplitudes(c, oq, pre, psi) for pre in prefixes])
+    u = random_uniform((B, 64), 9005)
+    key = random_uniform((B, 64), 9006)
+    idx, _ = oracle.frugal_sample(amps, n, 10.0, u, key)
+    ok = idx >= 0
+    assert ok.mean() > 0.95
+    ps = np.abs(amps[ok, idx[ok]]) ** 2
+    assert abs(oracle.linear_xeb(ps, n) - 1.0) < 0.2
+    # uniformly chosen candidates score about 0
+    pu = np.abs(amps[np.arange(B), (key[:, 0] * 64).astype(int)]) ** 2
+    assert abs(oracle.linear_xeb(pu, n)) < 0.2
+
