@@ -284,6 +284,25 @@ typedef struct {
 tn_status tn_plan_search(tn_network *net, const tn_plan_opts *base, const tn_search_opts *so,
                          tn_mlp *mlp, tn_precision prec, tn_plan **out, tn_search_report *report);
 
+/* Sec. 2 (after the frugal rejection sampling the paper cites as MFI+18):
+ * turn amplitude batches into samples. amps_dev holds n_batches x batch_size
+ * complex amplitudes (FP64 re, im interleaved; e.g. the 2^n_open amplitudes
+ * of one bitstring prefix per batch, as tn_contract_stem writes them).
+ * Candidate j of batch b is accepted when u[b][j] < 2^n_qubits p / M, p =
+ * re^2 + im^2 (acceptance probability min(1, 2^n p / M) for u uniform in
+ * [0, 1)), evaluated in FP64 without fused multiply-adds. The batch's sample
+ * is the accepted candidate with the smallest key[b][j] (a random visiting
+ * order), or -1. u_dev and key_dev are n_batches x batch_size doubles; the
+ * caller draws them, so results are reproducible. Outputs (device,
+ * caller-owned): index_dev[b], accepted_dev[b] (number accepted) and
+ * picked_dev[2b..2b+1] (the sampled amplitude, 0 if none). All pointers must
+ * be device memory (else TN_ERR_INVALID_ARG); 1 <= batch_size <= 2^20,
+ * 1 <= n_qubits <= 1000, M > 0. Asynchronous on cuda_stream. */
+tn_status tn_frugal_sample(const double *amps_dev, const double *u_dev, const double *key_dev,
+                           int64_t n_batches, int32_t batch_size, int32_t n_qubits, double M,
+                           void *cuda_stream, int32_t *index_dev, int32_t *accepted_dev,
+                           double *picked_dev);
+
 /* Sec. 2: linear XEB 2^n <p> - 1 of count amplitudes (interleaved re, im,
  * device memory), p = |amp|^2, computed in FP64 on the device. out is a host
  * double. Synchronises cuda_stream. */

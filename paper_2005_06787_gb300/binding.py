@@ -31,7 +31,7 @@ EXPORTED = [
     "tn_network_destroy", "tn_linear_xeb", "tn_permute", "tn_cgemm", "tn_last_error",
     "tn_version", "tn_plan_features", "tn_mlp_create", "tn_mlp_n_params", "tn_mlp_set_params",
     "tn_mlp_get_params", "tn_mlp_loss_grad", "tn_mlp_train", "tn_mlp_predict", "tn_mlp_destroy",
-    "tn_plan_search", "tn_set_prefix", "tn_destroy_plan", "tn_destroy_network",
+    "tn_plan_search", "tn_set_prefix", "tn_destroy_plan", "tn_destroy_network", "tn_frugal_sample",
 ]
 N_FEATURES = 16
 
@@ -123,6 +123,7 @@ def load():
     L.tn_network_destroy.restype = None
     L.tn_plan_profile.argtypes = [vp, u64, C.c_int, C.c_int, vp, vp, i32, vp]
     L.tn_linear_xeb.argtypes = [vp, i64, i32, vp, C.POINTER(C.c_double)]
+    L.tn_frugal_sample.argtypes = [vp, vp, vp, i64, i32, i32, C.c_double, vp, vp, vp, vp]
     L.tn_permute.argtypes = [vp, vp, i32, vp, vp]
     L.tn_cgemm.argtypes = [vp, vp, vp, i64, i64, i64, i64, i64, i64, i64, C.c_int, vp]
     L.tn_plan_features.argtypes = [vp, C.c_int, C.c_int, vp, vp, i32, vp]
@@ -360,6 +361,18 @@ def tn_linear_xeb(amps_dev, n_qubits: int, stream=None) -> float:
     count = amps_dev.numel() // 2
     _check(L.tn_linear_xeb(_ptr(amps_dev), count, n_qubits, _stream(stream), C.byref(out)))
     return out.value
+
+
+def tn_frugal_sample(amps_dev, u_dev, key_dev, n_batches: int, batch_size: int, n_qubits: int,
+                     M: float, index_dev, accepted_dev, picked_dev, stream=None):
+    """Frugal rejection sampling of n_batches amplitude batches (device
+    buffers: FP64 complex amplitudes and uniforms u, key of n_batches x
+    batch_size; outputs int32 index and accepted count per batch and the
+    sampled FP64 complex amplitude)."""
+    L = load()
+    _check(L.tn_frugal_sample(_ptr(amps_dev), _ptr(u_dev), _ptr(key_dev), n_batches, batch_size,
+                              n_qubits, float(M), _stream(stream), _ptr(index_dev),
+                              _ptr(accepted_dev), _ptr(picked_dev)))
 
 
 def tn_permute(inp, out, rank: int, perm: Sequence[int], stream=None):

@@ -352,6 +352,31 @@ tn_status tn_set_prefix(tn_network *net, const uint8_t *closed_bits) {
     });
 }
 
+tn_status tn_frugal_sample(const double *amps_dev, const double *u_dev, const double *key_dev,
+                           int64_t n_batches, int32_t batch_size, int32_t n_qubits, double M,
+                           void *cuda_stream, int32_t *index_dev, int32_t *accepted_dev,
+                           double *picked_dev) {
+    return guard([&] {
+        if (n_batches < 0 || batch_size < 1 || batch_size > (1 << 20) || n_qubits < 1 ||
+            n_qubits > 1000 || !(M > 0.0) || !std::isfinite(M))
+            tn::fail(TN_ERR_INVALID_ARG, "bad sampling size or threshold");
+        if (n_batches == 0) return;
+        const void *ptrs[] = {amps_dev, u_dev, key_dev, index_dev, accepted_dev, picked_dev};
+        for (const void *q : ptrs) {
+            cudaPointerAttributes a{};
+            if (!q || cudaPointerGetAttributes(&a, q) != cudaSuccess ||
+                (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)) {
+                cudaGetLastError();
+                tn::fail(TN_ERR_INVALID_ARG, "sampling buffers must be device memory");
+            }
+        }
+        TN_CUDA(tn::launch_frugal_sample(reinterpret_cast<const double2 *>(amps_dev), u_dev, key_dev,
+                                         n_batches, batch_size, n_qubits, M, index_dev, accepted_dev,
+                                         reinterpret_cast<double2 *>(picked_dev),
+                                         (cudaStream_t)cuda_stream));
+    });
+}
+
 tn_status tn_linear_xeb(const double *amps_dev, int64_t count, int32_t n_qubits,
                         void *cuda_stream, double *out) {
     return guard([&] {

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstddef>
 #include <cstdint>
 
@@ -600,6 +601,65 @@ cudaError_t launch_xeb_sum(const double2 *amps, int64_t n, double *out_sum, cuda
     const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(256, (n + 255) / 256));
     xeb_partial_kernel<<<nb, 256, 0, st>>>(amps, n, out_sum + 1);
     xeb_final_kernel<<<1, 1, 0, st>>>(out_sum + 1, nb, out_sum);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------- frugal sampling
+// Frugal rejection sampling (Sec. 2): one warp per batch of K candidate
+// amplitudes. Candidate j is accepted when u[j] < 2^n p / M with
+// p = re*re + im*im, each operation rounded on its own (no fused
+// multiply-add), so the decision matches an FP64 evaluation of the same
+// expression. The batch's sample is the accepted candidate with the smallest
+// key (a random visiting order; equal keys go to the lower j).
+__global__ void frugal_sample_kernel(const double2 *__restrict__ amps, const double *__restrict__ u,
+                                     const double *__restrict__ key, int64_t B, int K, double N,
+                                     double M, int32_t *__restrict__ idx, int32_t *__restrict__ cnt,
+                                     double2 *__restrict__ picked) {
+    const int64_t b = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (b >= B) return;  // uniform over the warp
+    const double2 *a = amps + b * K;
+    const double *ub = u + b * K, *kb = key + b * K;
+    double best_key = 0.0;
+    int best_j = -1, c = 0;
+    for (int j = lane; j < K; j += 32) {
+        const double2 v = a[j];
+        const double p = __dadd_rn(__dmul_rn(v.x, v.x), __dmul_rn(v.y, v.y));
+        const double thr = __ddiv_rn(__dmul_rn(p, N), M);
+        if (ub[j] < thr) {
+            ++c;
+            const double k = kb[j];
+            if (best_j < 0 || k < best_key) {  // j ascends per lane: ties keep the lower j
+                best_key = k;
+                best_j = j;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ok = __shfl_xor_sync(0xffffffffu, best_key, o);
+        const int oj = __shfl_xor_sync(0xffffffffu, best_j, o);
+        if (oj >= 0 && (best_j < 0 || ok < best_key || (ok == best_key && oj < best_j))) {
+            best_key = ok;
+            best_j = oj;
+        }
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    if (lane == 0) {
+        idx[b] = best_j;
+        cnt[b] = c;
+        picked[b] = best_j >= 0 ? a[best_j] : make_double2(0.0, 0.0);
+    }
+}
+
+cudaError_t launch_frugal_sample(const double2 *amps, const double *u, const double *key, int64_t B,
+                                 int K, int n_qubits, double M, int32_t *idx, int32_t *cnt,
+                                 double2 *picked, cudaStream_t st) {
+    if (B <= 0) return cudaSuccess;
+    const int threads = 256;
+    const int64_t blocks = (B * 32 + threads - 1) / threads;
+    frugal_sample_kernel<<<(unsigned)blocks, threads, 0, st>>>(amps, u, key, B, K, std::ldexp(1.0, n_qubits),
+                                                               M, idx, cnt, picked);
     return cudaGetLastError();
 }
 

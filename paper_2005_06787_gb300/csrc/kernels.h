@@ -61,6 +61,9 @@ cudaError_t launch_finalize(const double2 *sum, const double2 *comp, double2 *ou
 cudaError_t launch_xeb_sum(const double2 *amps, int64_t n, double *out_sum, cudaStream_t st);
 cudaError_t launch_permute(const float2 *in, float2 *out, int rank, const int *perm,
                            cudaStream_t st);
+cudaError_t launch_frugal_sample(const double2 *amps, const double *u, const double *key, int64_t B,
+                                 int K, int n_qubits, double M, int32_t *idx, int32_t *cnt,
+                                 double2 *picked, cudaStream_t st);
 
 bool tc_gemm_supported(int k, int n);
 cudaError_t tc_gemm_init();

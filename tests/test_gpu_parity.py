@@ -15,7 +15,7 @@ import pytest
 import oracle
 import paper_2005_06787_gb300 as P
 from synthetic.circuits import (CONFIGS, Circuit, config_circuit, grid_layout, random_bits,
-                                random_circuit, random_complex)
+                                random_circuit, random_complex, random_uniform)
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-5
@@ -249,6 +249,62 @@ def test_set_prefix_revalues_projectors_and_short_names():
     P.tn_destroy_plan(plan_a)
     P.tn_destroy_plan(plan_b)
     P.tn_destroy_network(net)
+
+
+# ------------------------------------------------------- frugal sampling
+
+def _sample_gpu(amps, n, M, u, key):
+    B, K = amps.shape
+    d_a = torch.from_numpy(np.ascontiguousarray(amps).view(np.float64).copy()).cuda()
+    d_u = torch.from_numpy(np.ascontiguousarray(u)).cuda()
+    d_k = torch.from_numpy(np.ascontiguousarray(key)).cuda()
+    idx = torch.empty(B, dtype=torch.int32, device="cuda")
+    cnt = torch.empty(B, dtype=torch.int32, device="cuda")
+    picked = torch.empty(2 * B, dtype=torch.float64, device="cuda")
+    P.tn_frugal_sample(d_a, d_u, d_k, B, K, n, M, idx, cnt, picked)
+    torch.cuda.synchronize()
+    pk = picked.cpu().numpy()
+    return idx.cpu().numpy(), cnt.cpu().numpy(), pk[0::2] + 1j * pk[1::2]
+
+
+@pytest.mark.parametrize("B,K,n,M", [(300, 64, 12, 10.0), (7, 256, 20, 3.0), (1000, 1, 5, 0.5),
+                                     (64, 100, 9, 40.0)])
+def test_frugal_sample_matches_oracle(B, K, n, M):
+    amps = random_complex((B, K), 40 + K) / math.sqrt(2.0 * 2 ** n)
+    u = random_uniform((B, K), 500 + K)
+    key = random_uniform((B, K), 600 + K)
+    idx, cnt, picked = _sample_gpu(amps, n, M, u, key)
+    ridx, rcnt = oracle.frugal_sample(amps, n, M, u, key)
+    assert (idx == ridx).all() and (cnt == rcnt).all()
+    ok = ridx >= 0
+    assert np.array_equal(picked[ok], amps[ok, ridx[ok]]) and (picked[~ok] == 0).all()
+
+
+def test_frugal_sampling_of_contracted_batches():
+    # 30 qubits, 16 prefixes x 64 open amplitudes contracted over all slices,
+    # then one sample per prefix batch; decisions match the oracle on the
+    # same amplitudes exactly, and the state vector's amplitudes wherever no
+    # candidate sits within 1e-4 of its threshold
+    name = "grid5x6_m14"
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "grid5x6_m14_amps.json")))
+    c = config_circuit(name)
+    oq = g["open_qubits"]
+    pres = np.asarray(g["prefixes"], dtype=np.uint8)
+    net, plan = _plan(c, oq, list(pres[0]), cw_limit=30, restarts=2)
+    P.tn_plan_prepare(plan, pres)
+    amps = run(plan, 0, 1 << P.tn_plan_info(plan)["n_sliced"])
+    n, M = c.n_qubits, 10.0
+    u = random_uniform(amps.shape, 7001)
+    key = random_uniform(amps.shape, 7002)
+    idx, cnt, _ = _sample_gpu(amps, n, M, u, key)
+    ridx, rcnt = oracle.frugal_sample(amps, n, M, u, key)
+    assert (idx == ridx).all() and (cnt == rcnt).all()
+    ref = np.asarray(g["amps_re"]) + 1j * np.asarray(g["amps_im"])
+    sidx, _ = oracle.frugal_sample(ref, n, M, u, key)
+    thr = np.abs(ref) ** 2 * 2.0 ** n / M
+    clear = (np.abs(u - thr) > 1e-4 * np.maximum(thr, 1e-300)).all(axis=1)
+    assert clear.sum() >= 12
+    assert (idx[clear] == sidx[clear]).all()
 
 
 # ------------------------------------------------------------ 30-qubit grid
