@@ -36,7 +36,7 @@ if ROOT not in sys.path:
 
 import numpy as np  # noqa: E402
 
-from synthetic.circuits import CONFIGS, config_circuit, random_bits  # noqa: E402
+from synthetic.circuits import CONFIGS, config_circuit, random_bits, random_uniform  # noqa: E402
 
 DEFAULT_WORKLOAD = "diag53_m14"
 METRIC = "stem TFLOP/s and slices/s at 53q/14-cycle, chosen vs plain FP32 at <=1e-5 rel err"
@@ -177,6 +177,52 @@ def dist_env():
     return rank, world, local
 
 
+def sampling_run(stream, job_seconds: float, n_open: int, M: float = 10.0):
+    """Sec. 2 frugal rejection sampling. Measured end to end on the 30-qubit
+    workload (16 prefixes x 64 amplitudes over all of its slices, then one
+    sample per prefix batch), and the bench workload's time per sample
+    extrapolated from its whole-batch time with the Porter-Thomas acceptance
+    probability of a batch: 1 - (1 - (1 - e^-M) / M)^(2^n_open)."""
+    import torch
+    import paper_2005_06787_gb300 as P
+    name = "grid5x6_m14"
+    cfg = CONFIGS[name]
+    c, oq, cb = workload_inputs(name)
+    pres = np.asarray([list(random_bits(c.n_qubits - len(oq), cfg["bit_seed"] + i))
+                       for i in range(cfg["prefixes"])], dtype=np.uint8)
+    net = P.tn_build_network(c, oq, list(pres[0]))
+    plan = P.tn_plan_create(net, **plan_options(name))
+    P.tn_plan_prepare(plan, pres, stream=stream)
+    nsl = P.tn_plan_info(plan)["n_sliced"]
+    B, K = len(pres), 1 << len(oq)
+    amps = torch.zeros(2 * B * K, dtype=torch.float64, device="cuda")
+    u = torch.from_numpy(random_uniform((B, K), 8101)).cuda()
+    key = torch.from_numpy(random_uniform((B, K), 8102)).cuda()
+    idx = torch.empty(B, dtype=torch.int32, device="cuda")
+    cnt = torch.empty(B, dtype=torch.int32, device="cuda")
+    picked = torch.empty(2 * B, dtype=torch.float64, device="cuda")
+    P.tn_contract_stem(plan, 0, 1 << nsl, amps, stream=stream)  # warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    P.tn_contract_stem(plan, 0, 1 << nsl, amps, stream=stream)
+    P.tn_frugal_sample(amps, u, key, B, K, c.n_qubits, M, idx, cnt, picked, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) / 1e3
+    got = idx.cpu().numpy()
+    pk = picked.cpu().numpy()
+    p_s = (pk[0::2] ** 2 + pk[1::2] ** 2)[got >= 0]
+    xeb = float((2.0 ** c.n_qubits) * p_s.mean() - 1.0) if len(p_s) else None
+    a = (1.0 - math.exp(-M)) / M
+    p_batch = 1.0 - (1.0 - a) ** (1 << n_open)
+    return {"M": M, "measured": {"workload": name, "batches": B, "samples": int((got >= 0).sum()),
+                                 "seconds": sec, "samples_per_s": float((got >= 0).sum()) / sec,
+                                 "xeb_of_samples": xeb},
+            "bench_workload_seconds_per_sample": job_seconds / p_batch,
+            "porter_thomas_accept_per_batch": p_batch}
+
+
 def run_reference(args):
     """The oracle arm: FP64 CPU contraction of bounded samples of the same
     workload (each step one bounded sample), same metric and units."""
@@ -312,6 +358,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--tile-bits", type=int, default=0)
     ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-sampling", action="store_true")
     ap.add_argument("--learned", action="store_true",
                     help="20-cycle learned-cost-model plan search instead of the default bench")
     ap.add_argument("--max-pass-steps", type=int, default=0)
@@ -503,6 +550,9 @@ def main():
                          f"first {done} of {len(order)} pairs in {secs:.1f} s"}
 
     launches_per_step = (info["n_passes_fused"] + info["n_gemm_steps"] + 2) + 1  # +finalize
+    samp = None
+    if rank == 0 and not args.no_sampling:
+        samp = sampling_run(stream, 2 ** info["n_sliced"] / slices_per_s, len(oq))
     if rank == 0:
         line = {
             "metric": METRIC, "value": tflops, "unit": "TFLOP/s",
@@ -527,6 +577,7 @@ def main():
                     "seconds": 2 ** info["n_sliced"] / slices_per_s,
                     "context": "paper Table 1, Sycamore-53 m=14 on one V100: 243.71 s, 2^10 "
                                "slices, tc 7.16e13 (another circuit and machine)"},
+            "sampling": samp,
             "roofline": roofline,
             "launch_breakdown": by_kind,
             "plain_breakdown": plain_kind,
