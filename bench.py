@@ -177,6 +177,27 @@ def dist_env():
     return rank, world, local
 
 
+# DRAM traffic of the dominant kernel, from one ncu capture of this bench's
+# launches (profiles/launches_diag53_m14.md: dram__bytes_read.sum +
+# dram__bytes_write.sum over the pass launches of one batch). It describes
+# the kernel source and plan it was taken on: with any other kernels.cu or
+# plan the bench reports traffic as null.
+TRAFFIC_CAPTURE = {"kernels_sha256": "e7de0f4d2606fe4a", "workload": "diag53_m14", "pass_launches": 43,
+                   "log2_tc_total": 50.304, "dram_bytes_per_batch": 50.02e9}
+
+
+def pass_traffic(name: str, info: dict):
+    import hashlib
+    src = os.path.join(ROOT, "paper_2005_06787_gb300", "csrc", "kernels.cu")
+    with open(src, "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    t = TRAFFIC_CAPTURE
+    if (sha != t["kernels_sha256"] or name != t["workload"] or info["n_passes_fused"] != t["pass_launches"]
+            or abs(info["log2_tc"] - t["log2_tc_total"]) > 1e-3):
+        return None
+    return t["dram_bytes_per_batch"] / t["pass_launches"]
+
+
 def sampling_run(stream, job_seconds: float, n_open: int, M: float = 10.0):
     """Sec. 2 frugal rejection sampling. Measured end to end on the 30-qubit
     workload (16 prefixes x 64 amplitudes over all of its slices, then one
@@ -494,7 +515,8 @@ def main():
     achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
     tot_ms = sum(v["ms"] for v in by_kind.values())
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": "pass_kernel",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": pass_traffic(name, info),
+                "algorithmic_bytes_per_launch": d["bytes"] / d["launches"], "kernel": "pass_kernel",
                 "peak_source": peak_kind, "share_of_step": d["ms"] / tot_ms if tot_ms else None,
                 "simt_tflops": d["flops"] / (d["ms"] / 1e3) / 1e12}
 
