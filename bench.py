@@ -45,7 +45,9 @@ METRIC = "stem TFLOP/s and slices/s at 53q/14-cycle, chosen vs plain FP32 at <=1
 def plan_options(name: str) -> dict:
     """Planner options of each workload (shared by the bench and its tests)."""
     cfg = CONFIGS[name]
-    o = dict(cw_limit=cfg.get("cw_limit") or 30, restarts=3, local_opt_iters=4, seed=0x5EED)
+    o = dict(cw_limit=cfg.get("cw_limit") or 30, restarts=2, local_opt_iters=4, seed=0x5EED)
+    if cfg["layout"][0] == "diag53":
+        o["anneal_iters"] = 600000
     if cfg.get("n_sliced"):
         o["min_sliced"] = cfg["n_sliced"]
     return o
