@@ -211,9 +211,15 @@ pass_kernel(const DevPass *__restrict__ gpass, const int *__restrict__ chunks,
     const unsigned my_fin = lane < (unsigned)nfree ? (unsigned)P.free_in[lane] : 0u;
     const unsigned my_fout = lane < (unsigned)nfree ? (unsigned)P.free_out[lane] : 0u;
     const int st_lo = P.st_lo[threadIdx.x & 63];
-    const int st_lo2 = P.st_lo[(2 * threadIdx.x) & 63];
     const bool st_pair = c_out >= 1 && P.st_lo[1] == 1;
     __syncthreads();
+    // per-thread parts of the load and paired-store offsets (idx = 2 tid + 512 j;
+    // the chunk tables are complete after the barrier above)
+    const int ld_i0 = 2 * threadIdx.x;
+    const int ld_off0 = (ld_i0 < tin_n) ? cin_tab[ld_i0 >> c_in] + (ld_i0 & cin_mask) : 0;
+    const int ld_sw0 = dev_swizzle(ld_i0);
+    const int st_off0 = (ld_i0 < tout_n) ? cout_tab[ld_i0 >> c_out] + (ld_i0 & cout_mask) : 0;
+    const int st_t0 = (ld_i0 < tout_n) ? (P.st_lo[ld_i0 & 63] ^ P.st_hi[ld_i0 >> 6]) : 0;
     // unit u -> (batch item, prefix, slice); invalid past the slice range
     const int SB = ba.SB;
     auto unit_item = [&](int64_t u, int &item, int &p, int64_t &s) {
@@ -236,8 +242,14 @@ pass_kernel(const DevPass *__restrict__ gpass, const int *__restrict__ chunks,
                                                : in + (int64_t)item * P.in_item_stride;
         src += ib;
         if (c_in >= 1) {
-            for (int idx = 2 * threadIdx.x; idx < tin_n; idx += 2 * PASS_THREADS)
-                cp_async16(dstb + dev_swizzle(idx), src + cin_tab[idx >> c_in] + (idx & cin_mask));
+            // idx = 2 tid + 512 j: the chunk table and the swizzle are linear
+            // over disjoint bits, so the thread's part is fixed per pass and
+            // each j adds one block-uniform term
+            if (ld_i0 < tin_n) {
+                const float2 *s0 = src + ld_off0;
+                for (int j = 0, idx = ld_i0; idx < tin_n; ++j, idx += 2 * PASS_THREADS)
+                    cp_async16(dstb + (ld_sw0 ^ dev_swizzle(j << 9)), s0 + cin_tab[(j << 9) >> c_in]);
+            }
         } else {
             for (int idx = threadIdx.x; idx < tin_n; idx += PASS_THREADS)
                 cp_async8(dstb + dev_swizzle(idx), src + cin_tab[idx >> c_in] + (idx & cin_mask));
@@ -278,9 +290,10 @@ pass_kernel(const DevPass *__restrict__ gpass, const int *__restrict__ chunks,
             float2 *dst = out + (int64_t)item * P.out_item_stride + ob;
             if (st_pair) {
                 // output bit 0 is tile position 0: entry pairs move as 16 bytes
-                for (int idx = 2 * threadIdx.x; idx < tout_n; idx += 2 * PASS_THREADS)
-                    *reinterpret_cast<float4 *>(dst + cout_tab[idx >> c_out] + (idx & cout_mask)) =
-                        *reinterpret_cast<const float4 *>(tile + (st_lo2 ^ P.st_hi[idx >> 6]));
+                float2 *d0 = dst + st_off0;
+                for (int j = 0, idx = ld_i0; idx < tout_n; ++j, idx += 2 * PASS_THREADS)
+                    *reinterpret_cast<float4 *>(d0 + cout_tab[(j << 9) >> c_out]) =
+                        *reinterpret_cast<const float4 *>(tile + (st_t0 ^ P.st_hi[j << 3]));
             } else {
                 for (int idx = threadIdx.x; idx < tout_n; idx += PASS_THREADS)
                     dst[cout_tab[idx >> c_out] + (idx & cout_mask)] = tile[st_lo ^ P.st_hi[idx >> 6]];
