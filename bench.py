@@ -184,8 +184,8 @@ def dist_env():
 # dram__bytes_write.sum over the pass launches of one batch). It describes
 # the kernel source and plan it was taken on: with any other kernels.cu or
 # plan the bench reports traffic as null.
-TRAFFIC_CAPTURE = {"kernels_sha256": "e7de0f4d2606fe4a", "workload": "diag53_m14", "pass_launches": 43,
-                   "log2_tc_total": 50.304, "dram_bytes_per_batch": 50.02e9}
+TRAFFIC_CAPTURE = {"kernels_sha256": "7db037e99de9d0c9", "workload": "diag53_m14", "pass_launches": 43,
+                   "log2_tc_total": 46.234, "dram_bytes_per_batch": 89.30e9}
 
 
 def pass_traffic(name: str, info: dict):
@@ -325,7 +325,7 @@ def run_learned(args):
     name = "diag53_m20"
     c, oq, cb = workload_inputs(name)
     net = P.tn_build_network(c, oq, cb)
-    base = dict(plan_options(name), max_sliced=60, restarts=1, anneal_iters=100000)
+    base = dict(plan_options(name), max_sliced=64, restarts=3, anneal_iters=100000)
     out = torch.zeros(2 * (1 << len(oq)), dtype=torch.float64, device="cuda")
     res = {}
     for label, m in (("mlp", mlp), ("flop", None)):

@@ -162,7 +162,12 @@ SearchResult plan_search(const Network &net, const tn_plan_opts &base, const tn_
     for (int sd = 0; sd < n_seeds; ++sd) {
         tn_plan_opts o = base;
         o.seed = base.seed + 7919ull * (uint64_t)sd;
-        Scheme sch = plan_scheme(net, o);
+        Scheme sch;
+        try {
+            sch = plan_scheme(net, o);
+        } catch (const Error &) {
+            continue;  // this stem-growth seed finds no scheme within the limits
+        }
         for (int mg : merges) {
             Scheme s2 = sch;
             if (mg >= 2) merge_branches(net, s2, mg, base.merge_rank_cap);

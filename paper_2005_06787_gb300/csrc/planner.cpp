@@ -567,28 +567,38 @@ Scheme plan_scheme(const Network &net, const tn_plan_opts &o) {
     for (int r = 0; r < restarts; ++r) {
         int seed = (r == 0) ? 0 : pick(rng);
         double noise = (r == 0) ? 0.0 : 0.9;
-        std::vector<int> order = grow_stem(B, seed, rng, noise);
-        Bits sliced(net.n_edges());
-        std::vector<int> sl;
-        anneal_order(B, seed, order, sliced, limit, anneal, rng);
-        local_opt_sweeps(B, seed, order, sliced, limit, lo_iters, 0);
-        bool ok = dynamic_slice(net, B, seed, order, sliced, sl, limit, o.min_sliced, max_sl,
-                                lo_iters, anneal / 10, rng);
-        if (!ok) continue;
-        anneal_order(B, seed, order, sliced, limit, anneal / 2, rng, 0.3, 0.01, 48, limit);
-        anneal_sliced(net, B, seed, order, sliced, sl, limit, o.min_sliced, anneal / 4, rng);
-        local_opt_sweeps(B, seed, order, sliced, limit, lo_iters, (int)sl.size());
-        StemEval ev = eval_stem(B, seed, order, sliced);
-        if (ev.max_rank > limit) continue;
-        double sc = scheme_score(ev, (int)sl.size(), limit);
-        if (sc < best_score) {
-            best_score = sc;
-            best.clusters = clusters;
-            best.seed_cluster = seed;
-            best.stem_order = order;
-            best.sliced = sliced;
-            best.sliced_list = sl;
-        }
+        const std::vector<int> grown = grow_stem(B, seed, rng, noise);
+        // one pipeline run; ann = annealing moves (0: greedy slicing and window
+        // optimisation only). Returns false when slicing misses the limit.
+        auto attempt = [&](long ann) {
+            std::vector<int> order = grown;
+            Bits sliced(net.n_edges());
+            std::vector<int> sl;
+            anneal_order(B, seed, order, sliced, limit, ann, rng);
+            local_opt_sweeps(B, seed, order, sliced, limit, lo_iters, 0);
+            if (!dynamic_slice(net, B, seed, order, sliced, sl, limit, o.min_sliced, max_sl, lo_iters,
+                               ann / 10, rng))
+                return false;
+            anneal_order(B, seed, order, sliced, limit, ann / 2, rng, 0.3, 0.01, 48, limit);
+            anneal_sliced(net, B, seed, order, sliced, sl, limit, o.min_sliced, ann / 4, rng);
+            local_opt_sweeps(B, seed, order, sliced, limit, lo_iters, (int)sl.size());
+            StemEval ev = eval_stem(B, seed, order, sliced);
+            if (ev.max_rank > limit) return false;
+            double sc = scheme_score(ev, (int)sl.size(), limit);
+            if (sc < best_score) {
+                best_score = sc;
+                best.clusters = clusters;
+                best.seed_cluster = seed;
+                best.stem_order = order;
+                best.sliced = sliced;
+                best.sliced_list = sl;
+            }
+            return true;
+        };
+        // an annealed stem can need more sliced edges than the budget allows
+        // (annealing between picks keeps the width, it does not force it
+        // down); the greedy pipeline is then tried on the same grown stem
+        if (!attempt(anneal) && anneal > 0) attempt(0);
     }
     if (best.seed_cluster < 0)
         fail(TN_ERR_PLAN_INFEASIBLE, "no scheme within the width limit and slice budget");
