@@ -119,6 +119,23 @@ def test_plan_shapes_of_paper_workloads():
     assert info["stem_bytes_fused"] < info["stem_bytes_plain"] / 4
 
 
+def test_annealing_planner_cost_on_12_cycles():
+    # Supp. A.2 local optimisation + dynamic slicing: the annealed search must
+    # keep the 53-qubit 12-cycle batch (64 amplitudes) within width 30 at a
+    # total cost near the paper's 1.09e13 = 2^43.3 (Table 1, Sycamore), and
+    # well below the greedy stem growth alone
+    name = "diag53_m12"
+    cfg = CONFIGS[name]
+    c = config_circuit(name)
+    oq = c.layout.open_qubits(cfg["n_open"])
+    net, _ = _net(c, oq, cfg["bit_seed"])
+    greedy = P.tn_plan_info(P.tn_plan_create(net, cw_limit=30, restarts=2, anneal_iters=-1))
+    annealed = P.tn_plan_info(P.tn_plan_create(net, cw_limit=30, restarts=2, anneal_iters=300000))
+    assert annealed["cw"] <= 30 and greedy["cw"] <= 30
+    assert annealed["log2_tc"] <= 44.5, annealed["log2_tc"]
+    assert annealed["log2_tc"] < greedy["log2_tc"] - 2.0
+
+
 def test_network_info_wire_segments():
     c = random_circuit(grid_layout(2, 2), 2, 9)
     net, _ = _net(c, [1], 3)
