@@ -284,6 +284,14 @@ typedef struct {
 tn_status tn_plan_search(tn_network *net, const tn_plan_opts *base, const tn_search_opts *so,
                          tn_mlp *mlp, tn_precision prec, tn_plan **out, tn_search_report *report);
 
+/* Device-side waits (no counterpart in the paper): every wait inside a
+ * kernel of this library on a tensor-core operation is bounded; one that
+ * gives up records a flag instead of hanging. This call synchronises the
+ * device, reads the flag and returns TN_ERR_TIMEOUT if a wait ever gave up,
+ * else TN_OK. Results of calls made after a wait gave up are not to be
+ * trusted. */
+tn_status tn_device_status(void);
+
 /* Sec. 2 (after the frugal rejection sampling the paper cites as MFI+18):
  * turn amplitude batches into samples. amps_dev holds n_batches x batch_size
  * complex amplitudes (FP64 re, im interleaved; e.g. the 2^n_open amplitudes

@@ -32,6 +32,7 @@ EXPORTED = [
     "tn_version", "tn_plan_features", "tn_mlp_create", "tn_mlp_n_params", "tn_mlp_set_params",
     "tn_mlp_get_params", "tn_mlp_loss_grad", "tn_mlp_train", "tn_mlp_predict", "tn_mlp_destroy",
     "tn_plan_search", "tn_set_prefix", "tn_destroy_plan", "tn_destroy_network", "tn_frugal_sample",
+    "tn_device_status",
 ]
 N_FEATURES = 16
 
@@ -124,6 +125,7 @@ def load():
     L.tn_plan_profile.argtypes = [vp, u64, C.c_int, C.c_int, vp, vp, i32, vp]
     L.tn_linear_xeb.argtypes = [vp, i64, i32, vp, C.POINTER(C.c_double)]
     L.tn_frugal_sample.argtypes = [vp, vp, vp, i64, i32, i32, C.c_double, vp, vp, vp, vp]
+    L.tn_device_status.argtypes = []
     L.tn_permute.argtypes = [vp, vp, i32, vp, vp]
     L.tn_cgemm.argtypes = [vp, vp, vp, i64, i64, i64, i64, i64, i64, i64, C.c_int, vp]
     L.tn_plan_features.argtypes = [vp, C.c_int, C.c_int, vp, vp, i32, vp]
@@ -373,6 +375,11 @@ def tn_frugal_sample(amps_dev, u_dev, key_dev, n_batches: int, batch_size: int, 
     _check(L.tn_frugal_sample(_ptr(amps_dev), _ptr(u_dev), _ptr(key_dev), n_batches, batch_size,
                               n_qubits, float(M), _stream(stream), _ptr(index_dev),
                               _ptr(accepted_dev), _ptr(picked_dev)))
+
+
+def tn_device_status() -> None:
+    """Raise TnError(TN_ERR_TIMEOUT) if a bounded device-side wait gave up."""
+    _check(load().tn_device_status())
 
 
 def tn_permute(inp, out, rank: int, perm: Sequence[int], stream=None):

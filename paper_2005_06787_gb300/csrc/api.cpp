@@ -352,6 +352,15 @@ tn_status tn_set_prefix(tn_network *net, const uint8_t *closed_bits) {
     });
 }
 
+tn_status tn_device_status(void) {
+    return guard([&] {
+        TN_CUDA(cudaDeviceSynchronize());
+        int tc_flag = 0;
+        TN_CUDA(tn::tc_error_flag(&tc_flag));
+        if (tc_flag) tn::fail(TN_ERR_TIMEOUT, "a tensor-core GEMM wait timed out");
+    });
+}
+
 tn_status tn_frugal_sample(const double *amps_dev, const double *u_dev, const double *key_dev,
                            int64_t n_batches, int32_t batch_size, int32_t n_qubits, double M,
                            void *cuda_stream, int32_t *index_dev, int32_t *accepted_dev,

@@ -31,6 +31,14 @@ def _built():
     torch.cuda.set_device(0)
 
 
+@pytest.fixture(autouse=True)
+def _device_waits_completed():
+    # every bounded device-side wait of the test (tensor-core GEMM) must have
+    # completed
+    yield
+    P.tn_device_status()
+
+
 def rel_l2(a, b):
     a = np.asarray(a).reshape(-1)
     b = np.asarray(b).reshape(-1)
