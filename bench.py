@@ -48,6 +48,10 @@ def plan_options(name: str) -> dict:
     o = dict(cw_limit=cfg.get("cw_limit") or 30, restarts=2, local_opt_iters=4, seed=0x5EED)
     if cfg["layout"][0] == "diag53":
         o["anneal_iters"] = 600000
+    if name == "diag53_m14":
+        # the best of eight planner seeds (0x5eed..0x5ef4, 2 restarts x 600 000
+        # annealing moves each): total cost 2^45.6 with 8 sliced edges
+        o["seed"] = 0x5EF3
     if cfg.get("n_sliced"):
         o["min_sliced"] = cfg["n_sliced"]
     return o
@@ -190,8 +194,8 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # dram__bytes_write.sum over the pass launches of one batch). It describes
 # the kernel source and plan it was taken on: with any other kernels.cu or
 # plan the bench reports traffic as null.
-TRAFFIC_CAPTURE = {"kernels_sha256": "7db037e99de9d0c9", "workload": "diag53_m14", "pass_launches": 43,
-                   "log2_tc_total": 46.234, "dram_bytes_per_batch": 89.30e9}
+TRAFFIC_CAPTURE = {"kernels_sha256": "7db037e99de9d0c9", "workload": "diag53_m14", "pass_launches": 44,
+                   "log2_tc_total": 45.640, "dram_bytes_per_batch": 145.03e9}
 
 
 def pass_traffic(name: str, info: dict):
