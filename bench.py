@@ -303,6 +303,86 @@ def _host_plan(name):
     return order, wires, P.tn_plan_info(plan)
 
 
+def run_configs(args):
+    """The other paper-shaped workloads, each on its own plan, FP32 fused path:
+    the 16-qubit batch of 64 closed bitstrings, the 30-qubit batch of 16
+    prefixes x 64 open amplitudes (all slices), and the 53-qubit 12-cycle
+    stem at four amplitude-batch shapes (2^0, 2^4, 2^6, 2^8 open amplitudes;
+    seeded slices timed, whole batch extrapolated). Inputs resident on the
+    device; CUDA-event timing after a warm-up run."""
+    import torch
+    import paper_2005_06787_gb300 as P
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    out_rows = []
+
+    def timed(plan, s0, s1, n_out, reps=2):
+        out = torch.zeros(2 * n_out, dtype=torch.float64, device="cuda")
+        P.tn_contract_stem(plan, s0, min(s1, s0 + 1), out, stream=stream)
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            P.tn_contract_stem(plan, s0, s1, out, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+        return best
+
+    # 16 qubits, 8 cycles: 64 closed bitstrings as 64 prefixes, one contraction
+    name = "grid4x4_m8"
+    cfg = CONFIGS[name]
+    c = config_circuit(name)
+    bits = np.asarray([list(random_bits(16, cfg["bit_seed"] + i)) for i in range(cfg["bitstrings"])],
+                      dtype=np.uint8)
+    net = P.tn_build_network(c, [], list(bits[0]))
+    plan = P.tn_plan_create(net, cw_limit=30, restarts=2)
+    P.tn_plan_prepare(plan, bits, stream=stream)
+    info = P.tn_plan_info(plan)
+    sec = timed(plan, 0, 1 << info["n_sliced"], len(bits))
+    out_rows.append({"workload": name, "amplitudes": len(bits), "n_sliced": info["n_sliced"],
+                     "seconds": sec, "amplitudes_per_s": len(bits) / sec})
+    # 30 qubits, 14 cycles: 16 prefixes x 64 open amplitudes over all slices
+    name = "grid5x6_m14"
+    cfg = CONFIGS[name]
+    c, oq, _ = workload_inputs(name)
+    pres = np.asarray([list(random_bits(c.n_qubits - len(oq), cfg["bit_seed"] + i))
+                       for i in range(cfg["prefixes"])], dtype=np.uint8)
+    net = P.tn_build_network(c, oq, list(pres[0]))
+    plan = P.tn_plan_create(net, **plan_options(name))
+    P.tn_plan_prepare(plan, pres, stream=stream)
+    info = P.tn_plan_info(plan)
+    sec = timed(plan, 0, 1 << info["n_sliced"], len(pres) << len(oq))
+    out_rows.append({"workload": name, "amplitudes": len(pres) << len(oq), "n_sliced": info["n_sliced"],
+                     "log2_tc_total": info["log2_tc"], "seconds": sec,
+                     "amplitudes_per_s": (len(pres) << len(oq)) / sec,
+                     # the plan's cost is per bitstring prefix; the batch holds len(pres)
+                     "stem_tflops": 8 * info["stem_tc_per_slice"] * len(pres) * (1 << info["n_sliced"]) / sec / 1e12})
+    # 53 qubits, 12 cycles at four batch shapes
+    name = "diag53_m12"
+    cfg = CONFIGS[name]
+    c = config_circuit(name)
+    for n_open in (0, 4, 6, 8):
+        oq = c.layout.open_qubits(n_open)
+        cb = list(random_bits(c.n_qubits - n_open, cfg["bit_seed"]))
+        net = P.tn_build_network(c, oq, cb)
+        plan = P.tn_plan_create(net, **dict(plan_options(name), anneal_iters=200000))
+        P.tn_plan_prepare(plan, stream=stream)
+        info = P.tn_plan_info(plan)
+        k = min(8, 1 << info["n_sliced"])
+        sec = timed(plan, 0, k, 1 << n_open) / k
+        out_rows.append({"workload": name, "n_open": n_open, "amplitudes": 1 << n_open, "cw": info["cw"],
+                         "n_sliced": info["n_sliced"], "log2_tc_total": info["log2_tc"],
+                         "ms_per_slice": sec * 1e3, "slices_per_s": 1 / sec,
+                         "stem_tflops": 8 * info["stem_tc_per_slice"] / sec / 1e12,
+                         "batch_seconds": sec * (1 << info["n_sliced"])})
+        del plan
+        torch.cuda.empty_cache()
+    print(json.dumps({"metric": "paper-shaped workloads, FP32 fused path, each on its own plan",
+                      "configs": out_rows, "data": "synthetic", "n_gpus": 1}), flush=True)
+
+
 def run_learned(args):
     """20-cycle workload: plan search scored by the learned MLP (trained on
     launch timings of the 30-qubit and 53-qubit 12/14-cycle workloads) versus
@@ -392,6 +472,8 @@ def main():
     ap.add_argument("--tile-bits", type=int, default=0)
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-sampling", action="store_true")
+    ap.add_argument("--configs", action="store_true",
+                    help="time the 16-qubit, 30-qubit and 53q/12-cycle workloads (four batch shapes)")
     ap.add_argument("--learned", action="store_true",
                     help="20-cycle learned-cost-model plan search instead of the default bench")
     ap.add_argument("--max-pass-steps", type=int, default=0)
@@ -406,6 +488,9 @@ def main():
         return
     if args.learned:
         run_learned(args)
+        return
+    if args.configs:
+        run_configs(args)
         return
 
     import torch
