@@ -266,7 +266,7 @@ void tn_mlp_destroy(tn_mlp *m);
 
 typedef struct {
     int32_t n_seeds;        /* stem-growth seeds (each gives 3 x 5 x 3 variants) */
-    double judge_factor;    /* fall back if the MLP pick's plain-model time exceeds
+    double fallback_factor;    /* fall back if the MLP pick's plain-model time exceeds
                                this factor times the plain model's best (0 = 4) */
 } tn_search_opts;
 

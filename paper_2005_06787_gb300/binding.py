@@ -81,7 +81,7 @@ class tn_launch_record(C.Structure):
 
 
 class tn_search_opts(C.Structure):
-    _fields_ = [("n_seeds", C.c_int32), ("judge_factor", C.c_double)]
+    _fields_ = [("n_seeds", C.c_int32), ("fallback_factor", C.c_double)]
 
 
 class tn_search_report(C.Structure):
@@ -470,11 +470,11 @@ class Mlp:
 
 
 def tn_plan_search(net: Network, mlp: Optional[Mlp] = None, prec: str = "fp32", n_seeds: int = 3,
-                   judge_factor: float = 4.0, **opts):
+                   fallback_factor: float = 4.0, **opts):
     """Search candidate plans; returns (plan, report dict)."""
     L = load()
     o = make_opts(**opts)
-    so = tn_search_opts(n_seeds, judge_factor)
+    so = tn_search_opts(n_seeds, fallback_factor)
     rep = tn_search_report()
     h = C.c_void_p()
     _check(L.tn_plan_search(net.handle, C.byref(o), C.byref(so), mlp.handle if mlp else None,

@@ -9,7 +9,7 @@
 // candidate plans (stem-growth seeds x tile size x steps per pass x branch
 // merging), scores every launch of every candidate with the MLP in one
 // batched GPU inference, and keeps the MLP's pick unless the FLOP-and-memory
-// model judges it much worse than its own pick (then it falls back).
+// model rates it much worse than its own pick (then it falls back).
 #include <algorithm>
 #include <cmath>
 #include <memory>
@@ -230,10 +230,10 @@ SearchResult plan_search(const Network &net, const tn_plan_opts &base, const tn_
     res.mlp_pick_flop_ms = flop_total[mlp_pick];
     res.flop_pick_mlp_ms = mlp ? mlp_total[flop_pick] : 0;
     res.mlp_pick_mlp_ms = mlp ? mlp_total[mlp_pick] : 0;
-    // the plain model judges the learned pick: beyond the allowed factor the
+    // the plain model checks the learned pick: beyond the allowed factor the
     // search falls back to the plain model's own pick
-    const double judge = so.judge_factor > 0 ? so.judge_factor : 4.0;
-    res.used_mlp = mlp && flop_total[mlp_pick] <= judge * flop_total[flop_pick];
+    const double allow = so.fallback_factor > 0 ? so.fallback_factor : 4.0;
+    res.used_mlp = mlp && flop_total[mlp_pick] <= allow * flop_total[flop_pick];
     const size_t pick = res.used_mlp ? mlp_pick : flop_pick;
     res.opts = cands[pick].opts;
     res.scheme = std::move(cands[pick].scheme);

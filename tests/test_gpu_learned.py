@@ -3,7 +3,7 @@
 The library's forward/backward kernels are checked against the FP64 oracle
 MLP (oracle/mlp.py) on the same parameters and rows; training must fit a known
 function; and the search scored by the trained network, with the plain
-FLOP-and-memory model as fallback and judge, must pick a plan at least as fast
+FLOP-and-memory model as fallback and check, must pick a plan at least as fast
 (measured on the GPU) as the plain model's own pick, on the 53-qubit 12-cycle
 workload with the network trained on that method's own step timings.
 """
