@@ -47,11 +47,8 @@ def plan_options(name: str) -> dict:
     cfg = CONFIGS[name]
     o = dict(cw_limit=cfg.get("cw_limit") or 30, restarts=2, local_opt_iters=4, seed=0x5EED)
     if cfg["layout"][0] == "diag53":
-        o["anneal_iters"] = 600000
-    if name == "diag53_m14":
-        # the best of eight planner seeds (0x5eed..0x5ef4, 2 restarts x 600 000
-        # annealing moves each): total cost 2^45.6 with 8 sliced edges
-        o["seed"] = 0x5EF3
+        # six annealed stems, the best two sliced and refined
+        o.update(anneal_iters=600000, restarts=6, slice_restarts=2)
     if cfg.get("n_sliced"):
         o["min_sliced"] = cfg["n_sliced"]
     return o
@@ -415,7 +412,7 @@ def run_learned(args):
     name = "diag53_m20"
     c, oq, cb = workload_inputs(name)
     net = P.tn_build_network(c, oq, cb)
-    base = dict(plan_options(name), max_sliced=64, restarts=3, anneal_iters=100000)
+    base = dict(plan_options(name), max_sliced=64, restarts=3, anneal_iters=100000, slice_restarts=0)
     out = torch.zeros(2 * (1 << len(oq)), dtype=torch.float64, device="cuda")
     res = {}
     for label, m in (("mlp", mlp), ("flop", None)):

@@ -98,6 +98,9 @@ typedef struct {
     int32_t anneal_iters;     /* simulated-annealing moves on the stem order per
                                  restart (0 = auto: 600 per branch cluster, at
                                  most 200000; < 0 = none) */
+    int32_t slice_restarts;   /* slice and refine only this many of the restarts'
+                                 annealed stems, the best by unsliced cost plus
+                                 width excess (0 = all) */
     uint64_t seed;
 } tn_plan_opts;
 

@@ -564,41 +564,87 @@ Scheme plan_scheme(const Network &net, const tn_plan_opts &o) {
     }
     // seeds: spread over clusters deterministically, the rest random
     std::uniform_int_distribution<int> pick(0, C - 1);
-    for (int r = 0; r < restarts; ++r) {
-        int seed = (r == 0) ? 0 : pick(rng);
-        double noise = (r == 0) ? 0.0 : 0.9;
-        const std::vector<int> grown = grow_stem(B, seed, rng, noise);
-        // one pipeline run; ann = annealing moves (0: greedy slicing and window
-        // optimisation only). Returns false when slicing misses the limit.
-        auto attempt = [&](long ann) {
-            std::vector<int> order = grown;
-            Bits sliced(net.n_edges());
-            std::vector<int> sl;
-            anneal_order(B, seed, order, sliced, limit, ann, rng);
-            local_opt_sweeps(B, seed, order, sliced, limit, lo_iters, 0);
-            if (!dynamic_slice(net, B, seed, order, sliced, sl, limit, o.min_sliced, max_sl, lo_iters,
-                               ann / 10, rng))
-                return false;
-            anneal_order(B, seed, order, sliced, limit, ann / 2, rng, 0.3, 0.01, 48, limit);
-            anneal_sliced(net, B, seed, order, sliced, sl, limit, o.min_sliced, ann / 4, rng);
-            local_opt_sweeps(B, seed, order, sliced, limit, lo_iters, (int)sl.size());
-            StemEval ev = eval_stem(B, seed, order, sliced);
-            if (ev.max_rank > limit) return false;
-            double sc = scheme_score(ev, (int)sl.size(), limit);
-            if (sc < best_score) {
-                best_score = sc;
-                best.clusters = clusters;
-                best.seed_cluster = seed;
-                best.stem_order = order;
-                best.sliced = sliced;
-                best.sliced_list = sl;
-            }
-            return true;
+    auto consider = [&](int seed, const std::vector<int> &order, const Bits &sliced,
+                        const std::vector<int> &sl) {
+        StemEval ev = eval_stem(B, seed, order, sliced);
+        if (ev.max_rank > limit) return false;
+        double sc = scheme_score(ev, (int)sl.size(), limit);
+        if (sc < best_score) {
+            best_score = sc;
+            best.clusters = clusters;
+            best.seed_cluster = seed;
+            best.stem_order = order;
+            best.sliced = sliced;
+            best.sliced_list = sl;
+        }
+        return true;
+    };
+    // slicing and refinement of one annealed order: dynamic slicing with an
+    // anneal after every pick, an order anneal that may not widen, the joint
+    // order / sliced-set anneal, window optimisation. False when slicing
+    // misses the limit.
+    auto slice_refine = [&](int seed, std::vector<int> order, long ann) {
+        Bits sliced(net.n_edges());
+        std::vector<int> sl;
+        if (!dynamic_slice(net, B, seed, order, sliced, sl, limit, o.min_sliced, max_sl, lo_iters, ann / 10,
+                           rng))
+            return false;
+        anneal_order(B, seed, order, sliced, limit, ann / 2, rng, 0.3, 0.01, 48, limit);
+        anneal_sliced(net, B, seed, order, sliced, sl, limit, o.min_sliced, ann / 4, rng);
+        local_opt_sweeps(B, seed, order, sliced, limit, lo_iters, (int)sl.size());
+        return consider(seed, order, sliced, sl);
+    };
+    // unsliced anneal + window optimisation of a grown stem
+    auto shape = [&](int seed, std::vector<int> order, long ann) {
+        Bits none(net.n_edges());
+        anneal_order(B, seed, order, none, limit, ann, rng);
+        local_opt_sweeps(B, seed, order, none, limit, lo_iters, 0);
+        return order;
+    };
+    if (o.slice_restarts <= 0 || o.slice_restarts >= restarts) {
+        // every restart grows, anneals, slices and refines in turn; an annealed
+        // stem can need more sliced edges than the budget allows (annealing
+        // between picks keeps the width, it does not force it down), and the
+        // greedy pipeline is then tried on the same grown stem
+        for (int r = 0; r < restarts; ++r) {
+            const int seed = (r == 0) ? 0 : pick(rng);
+            const double noise = (r == 0) ? 0.0 : 0.9;
+            const std::vector<int> grown = grow_stem(B, seed, rng, noise);
+            if (!slice_refine(seed, shape(seed, grown, anneal), anneal) && anneal > 0)
+                slice_refine(seed, shape(seed, grown, 0), 0);
+        }
+    } else {
+        // Phase 1: every restart grows a stem and anneals its order without
+        // slicing (score: log2 stem cost + one unit per bit above the width
+        // limit). Phase 2: only the best slice_restarts of them are sliced and
+        // refined, which costs more than phase 1, so more restarts widen the
+        // search at little extra cost. (The unsliced score predicts the
+        // sliced cost well when slicing removes a few bits of width; when it
+        // must remove many, slice every restart.)
+        struct Start {
+            double score;
+            int seed;
+            std::vector<int> grown, order;
         };
-        // an annealed stem can need more sliced edges than the budget allows
-        // (annealing between picks keeps the width, it does not force it
-        // down); the greedy pipeline is then tried on the same grown stem
-        if (!attempt(anneal) && anneal > 0) attempt(0);
+        std::vector<Start> starts;
+        for (int r = 0; r < restarts; ++r) {
+            Start st;
+            st.seed = (r == 0) ? 0 : pick(rng);
+            const double noise = (r == 0) ? 0.0 : 0.9;
+            st.grown = grow_stem(B, st.seed, rng, noise);
+            st.order = shape(st.seed, st.grown, anneal);
+            Bits none(net.n_edges());
+            st.score = scheme_score(eval_stem(B, st.seed, st.order, none), 0, limit);
+            starts.push_back(std::move(st));
+        }
+        std::stable_sort(starts.begin(), starts.end(),
+                         [](const Start &a, const Start &b) { return a.score < b.score; });
+        const int keep = std::min<int>((int)starts.size(), o.slice_restarts);
+        for (int r = 0; r < keep; ++r) {
+            const Start &st = starts[(size_t)r];
+            if (!slice_refine(st.seed, st.order, anneal) && anneal > 0)
+                slice_refine(st.seed, shape(st.seed, st.grown, 0), 0);
+        }
     }
     if (best.seed_cluster < 0)
         fail(TN_ERR_PLAN_INFEASIBLE, "no scheme within the width limit and slice budget");
