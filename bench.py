@@ -385,6 +385,33 @@ def run_configs(args):
                       "configs": out_rows, "data": "synthetic", "n_gpus": 1}), flush=True)
 
 
+def train_step_model(stream, workloads, precs_for_gemm=("fp32", "tf32x3")):
+    """Train the learned step-time model on this GPU: launch timings of plan
+    variants (tile size x steps per pass x branch merging, planned without
+    annealing) of the given workloads, one row per kernel launch."""
+    import torch
+    import paper_2005_06787_gb300 as P
+    from paper_2005_06787_gb300 import learned
+    t_start = time.perf_counter()
+    rows = []
+    for wl in workloads:
+        c, oq, cb = workload_inputs(wl)
+        net = P.tn_build_network(c, oq, cb)
+        for plan in learned.plan_variants(net, dict(plan_options(wl), anneal_iters=-1, restarts=1),
+                                          tiles=(11, 12), steps=(4, 8), merges=(0, 3)):
+            P.tn_plan_prepare(plan, stream=stream)
+            precs = precs_for_gemm if P.tn_plan_info(plan)["n_gemm_steps"] else ("fp32",)
+            for prec in precs:
+                rows.append(learned.profile_rows(plan, prec, "fused", repeats=2))
+            del plan
+            torch.cuda.empty_cache()
+    X = np.concatenate([r[0] for r in rows])
+    y = np.concatenate([r[1] for r in rows])
+    mlp = learned.train_cost_model(X, y, epochs=600)
+    fit = float(np.corrcoef(mlp.predict(X), y)[0, 1])
+    return mlp, int(len(y)), fit, time.perf_counter() - t_start
+
+
 def run_learned(args):
     """20-cycle workload: plan search scored by the learned MLP (trained on
     launch timings of the 30-qubit and 53-qubit 12/14-cycle workloads) versus
@@ -396,24 +423,7 @@ def run_learned(args):
     from synthetic.circuits import SplitMix64
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
-    t_start = time.perf_counter()
-    rows = []
-    for wl in ("grid5x6_m14", "diag53_m12", "diag53_m14"):
-        c, oq, cb = workload_inputs(wl)
-        net = P.tn_build_network(c, oq, cb)
-        for plan in learned.plan_variants(net, dict(plan_options(wl), anneal_iters=-1), tiles=(11, 12), steps=(4, 8),
-                                          merges=(0, 3)):
-            P.tn_plan_prepare(plan, stream=stream)
-            precs = ("fp32", "tf32x3") if P.tn_plan_info(plan)["n_gemm_steps"] else ("fp32",)
-            for prec in precs:
-                rows.append(learned.profile_rows(plan, prec, "fused", repeats=2))
-            del plan
-            torch.cuda.empty_cache()
-    X = np.concatenate([r[0] for r in rows])
-    y = np.concatenate([r[1] for r in rows])
-    mlp = learned.train_cost_model(X, y, epochs=600)
-    fit = float(np.corrcoef(mlp.predict(X), y)[0, 1])
-    train_s = time.perf_counter() - t_start
+    mlp, n_rows, fit, train_s = train_step_model(stream, ("grid5x6_m14", "diag53_m12", "diag53_m14"))
     name = "diag53_m20"
     c, oq, cb = workload_inputs(name)
     net = P.tn_build_network(c, oq, cb)
@@ -453,7 +463,7 @@ def run_learned(args):
     line = {"metric": "20-cycle plan chosen by learned vs plain cost model: extrapolated time "
                       "(64 seeded slices timed)", "value": res["mlp"]["extrapolated_days_all_slices"],
             "unit": "days", "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
-            "config": {"workload": name, "train_rows": int(len(y)), "train_fit_corr": fit,
+            "config": {"workload": name, "train_rows": n_rows, "train_fit_corr": fit,
                        "train_seconds": train_s},
             "mlp": res["mlp"], "flop": res["flop"],
             "gain_vs_flop_model": res["flop"]["extrapolated_days_all_slices"] / res["mlp"]["extrapolated_days_all_slices"]}
@@ -474,6 +484,9 @@ def main():
     ap.add_argument("--tile-bits", type=int, default=0)
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-sampling", action="store_true")
+    ap.add_argument("--plain-plan", action="store_true",
+                    help="plan with the planner's options only (no learned plan search)")
+    ap.add_argument("--search-seeds", type=int, default=4)
     ap.add_argument("--configs", action="store_true",
                     help="time the 16-qubit, 30-qubit and 53q/12-cycle workloads (four batch shapes)")
     ap.add_argument("--learned", action="store_true",
@@ -516,7 +529,27 @@ def main():
         popts["tile_bits"] = args.tile_bits
     if args.max_pass_steps:
         popts["max_pass_steps"] = args.max_pass_steps
-    plan = P.tn_plan_create(net, **popts)
+    choice = None
+    if world == 1 and not args.plain_plan and not (args.tile_bits or args.max_pass_steps):
+        # the chosen form's plan: candidates (stem-growth seeds x tile size x
+        # steps per pass x branch merging) scored by the learned step-time
+        # model trained on this GPU, the plain model as fallback; search seed
+        # 0 is the plan the plain planner gives for these options
+        mlp, n_rows, fit, train_s = train_step_model(stream, ("diag53_m12", "diag53_m14"),
+                                                     precs_for_gemm=("fp32",))
+        ts = time.perf_counter()
+        plan, rep = P.tn_plan_search(net, mlp=mlp, n_seeds=args.search_seeds, **popts)
+        choice = {"by": "learned model" if rep["used_mlp"] else "plain model (fallback)",
+                  "candidates": rep["n_candidates"], "launch_rows_scored": rep["n_launch_rows"],
+                  "pick": {k: rep["chosen"][k] for k in ("seed", "tile_bits", "max_pass_steps", "merge_group")},
+                  "plain_model_pick": {k: rep["flop_pick"][k] for k in ("seed", "tile_bits", "max_pass_steps",
+                                                                         "merge_group")},
+                  "predicted_job_s_mlp": rep["mlp_pick_mlp_ms"] / 1e3,
+                  "train_rows": n_rows, "train_fit_corr": fit, "train_seconds": train_s,
+                  "search_seconds": time.perf_counter() - ts}
+        del mlp
+    else:
+        plan = P.tn_plan_create(net, **popts)
     plan_s = time.perf_counter() - t0
     P.tn_plan_prepare(plan, stream=stream)
     torch.cuda.synchronize()
@@ -708,7 +741,8 @@ def main():
                        "slices_per_step": SB, "stem_tc_per_slice": info["stem_tc_per_slice"],
                        "log2_tc_total": info["log2_tc"],
                        "l2": "inputs larger than L2 (stem tensors up to 8 GiB)",
-                       "parallelism": f"slice ranges per GPU x{world}", "plan_seconds": plan_s},
+                       "parallelism": f"slice ranges per GPU x{world}", "plan_seconds": plan_s,
+                       "plan_choice": choice},
             "plain_fp32": {"value": plain_tflops, "unit": "TFLOP/s", "slices_per_s": plain_sps,
                            "steps": plain_steps},
             "speedup_vs_plain": slices_per_s / plain_sps / world if plain_sps else None,
