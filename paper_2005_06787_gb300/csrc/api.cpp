@@ -413,6 +413,35 @@ tn_status tn_permute(const float *in, float *out, int32_t rank, const int32_t *p
             if (perm[j] < 0 || perm[j] >= rank || seen[(size_t)perm[j]]++)
                 tn::fail(TN_ERR_INVALID_ARG, "perm is not a permutation");
         }
+        cudaStream_t st = (cudaStream_t)cuda_stream;
+        if (rank >= 4 && !(((uintptr_t)in | (uintptr_t)out) & 15)) {
+            // tiles of 128-byte chunks through shared memory (the fused pass
+            // kernel with no stem step): coalesced 16-byte reads and writes,
+            // which need 16-byte aligned tensors
+            std::vector<int> chunks;
+            const tn::DevPass P = tn::make_permute_pass(rank, std::vector<int>(perm, perm + rank), chunks);
+            TN_CUDA(tn::init_kernels());
+            unsigned char *d = nullptr;
+            const size_t cb = (chunks.size() * sizeof(int) + 255) & ~(size_t)255;
+            TN_CUDA(cudaMallocAsync((void **)&d, sizeof(tn::DevPass) + cb + sizeof(tn::DevState), st));
+            auto *d_pass = reinterpret_cast<tn::DevPass *>(d);
+            auto *d_chunks = reinterpret_cast<int *>(d + sizeof(tn::DevPass));
+            auto *d_state = reinterpret_cast<tn::DevState *>(d + sizeof(tn::DevPass) + cb);
+            const tn::DevState h_state{0, 1, 0, 0};
+            cudaError_t e = cudaMemcpyAsync(d_pass, &P, sizeof(P), cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(d_chunks, chunks.data(), chunks.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(d_state, &h_state, sizeof(h_state), cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess)
+                e = tn::launch_pass(d_pass, P, d_chunks, nullptr, nullptr, nullptr,
+                                    reinterpret_cast<const float2 *>(in), reinterpret_cast<float2 *>(out),
+                                    tn::BatchArgs{d_state, 1, 1, 0}, st);
+            cudaFreeAsync(d, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            TN_CUDA(e);
+            return;
+        }
         std::vector<int> tab(4 * 256, 0);
         for (int b = 0; b < 4; ++b)
             for (int v = 0; v < 256; ++v) {
@@ -423,7 +452,6 @@ tn_status tn_permute(const float *in, float *out, int32_t rank, const int32_t *p
                 }
                 tab[(size_t)(b * 256 + v)] = (int)o;
             }
-        cudaStream_t st = (cudaStream_t)cuda_stream;
         int *d_tab = nullptr;
         TN_CUDA(cudaMallocAsync((void **)&d_tab, tab.size() * sizeof(int), st));
         cudaError_t e = cudaMemcpyAsync(d_tab, tab.data(), tab.size() * sizeof(int),

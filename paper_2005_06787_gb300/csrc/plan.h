@@ -12,6 +12,9 @@
 namespace tn {
 
 BuiltStem build_stem_plan(const Network &net, const Scheme &s, const tn_plan_opts &o);
+// A pure-permutation pass (input bit j -> output bit perm[j]) for a rank-r
+// tensor, its chunk table appended to chunks; validated.
+DevPass make_permute_pass(int rank, const std::vector<int> &perm, std::vector<int> &chunks);
 
 // ---- cost models and search (costmodel.cpp, mlp.cu)
 constexpr int N_FEATURES = TN_N_FEATURES;

@@ -385,6 +385,20 @@ std::set<int> permute_tile(const std::vector<int> &lay, const std::vector<int> &
 
 }  // namespace
 
+DevPass make_permute_pass(int rank, const std::vector<int> &perm, std::vector<int> &chunks) {
+    // input bit j holds "edge" j; output bit perm[j] receives it
+    std::vector<int> Lin((size_t)rank), Lout((size_t)rank);
+    for (int j = 0; j < rank; ++j) {
+        Lin[(size_t)j] = j;
+        Lout[(size_t)perm[(size_t)j]] = j;
+    }
+    const int c = std::min(4, rank);
+    std::set<int> tile = permute_tile(Lin, Lout, c, 11);
+    DevPass P = build_pass(Lin, Lout, c, c, tile, {}, {}, {}, chunks);
+    validate_pass(P, chunks);
+    return P;
+}
+
 BuiltStem build_stem_plan(const Network &net, const Scheme &s, const tn_plan_opts &o) {
     BuiltStem R;
     const int T_MAX = (o.tile_bits > 0) ? std::min(o.tile_bits, MAX_TILE_BITS) : 12;

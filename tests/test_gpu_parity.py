@@ -57,13 +57,19 @@ def run(plan, s0, s1, mode="fused", prec="fp32", device=True, accumulate=False, 
 
 # ------------------------------------------------------------------ kernels
 
-@pytest.mark.parametrize("rank,seed", [(1, 1), (5, 2), (11, 3), (17, 4), (20, 5)])
-def test_permute_bit_exact(rank, seed):
+@pytest.mark.parametrize("rank,seed,offset", [(1, 1, 0), (4, 6, 0), (5, 2, 0), (11, 3, 0), (12, 7, 0),
+                                              (17, 4, 0), (20, 5, 0), (24, 8, 0), (13, 9, 1)])
+def test_permute_bit_exact(rank, seed, offset):
+    # rank >= 4 on 16-byte aligned tensors runs tiled through shared memory;
+    # an 8-byte offset (offset = 1 entry) takes the element-wise kernel
     rng = np.random.default_rng(seed)
     perm = rng.permutation(rank).astype(np.int32)
     x = random_complex((1 << rank,), seed, np.complex64)
-    xin = torch.from_numpy(x.view(np.float32).copy()).cuda()
-    xout = torch.empty_like(xin)
+    buf_in = torch.zeros(2 * ((1 << rank) + offset), dtype=torch.float32, device="cuda")
+    buf_out = torch.zeros_like(buf_in)
+    xin = buf_in[2 * offset:]
+    xin.copy_(torch.from_numpy(x.view(np.float32).copy()))
+    xout = buf_out[2 * offset:]
     P.tn_permute(xin, xout, rank, perm)
     torch.cuda.synchronize()
     got = xout.cpu().numpy().view(np.complex64)
