@@ -136,6 +136,27 @@ def test_annealing_planner_cost_on_12_cycles():
     assert annealed["log2_tc"] < greedy["log2_tc"] - 2.0
 
 
+def test_two_phase_restarts_give_valid_schemes():
+    # slice_restarts: every restart's stem is annealed unsliced, only the best
+    # ones are sliced; the scheme must still meet the width and its value
+    # must equal the state vector's
+    c = random_circuit(grid_layout(3, 4), 8, 91)
+    oq = [0, 7]
+    net, cb = _net(c, oq, 23)
+    plan = P.tn_plan_create(net, cw_limit=6, restarts=4, slice_restarts=1, anneal_iters=20000)
+    info = P.tn_plan_info(plan)
+    assert info["cw"] <= 6
+    order, sl = P.tn_plan_export(plan)
+    edges = _oracle_edges(net)
+    onet = oracle.build_network(c, oq, cb)
+    sliced = [edges[e] for e in sl]
+    tot = oracle.contract_sliced_sum(onet, sliced, [tuple(x) for x in order])
+    np.testing.assert_allclose(tot.reshape(-1), oracle.sv_amplitudes(c, oq, cb), atol=1e-13)
+    tc, ocw = oracle.tree_cost(onet.edges, onet.open_edges, [tuple(x) for x in order], sliced)
+    assert ocw == info["cw"]
+    assert math.log2(tc) == pytest.approx(info["log2_tc"], abs=1e-9)
+
+
 def test_network_info_wire_segments():
     c = random_circuit(grid_layout(2, 2), 2, 9)
     net, _ = _net(c, [1], 3)
