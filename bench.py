@@ -725,7 +725,9 @@ def main():
                "sample": f"FP64 pairwise contractions of slice 0 along the plan's order: "
                          f"first {done} of {len(order)} pairs in {secs:.1f} s"}
 
-    launches_per_step = (info["n_passes_fused"] + info["n_gemm_steps"] + 2) + 1  # +finalize
+    # passes, GEMM steps, accumulate, advance, finalize, and one staging
+    # kernel before each pass that reads its branch matrices from the constant bank
+    launches_per_step = (info["n_passes_fused"] + info["n_gemm_steps"] + 2) + 1 + info["n_passes_cbank"]
     samp = None
     if rank == 0 and not args.no_sampling:
         samp = sampling_run(stream, 2 ** info["n_sliced"] / slices_per_s, len(oq))

@@ -121,6 +121,12 @@ typedef struct {
     double stem_bytes_fused;  /* algorithmic HBM bytes per slice, fused mode */
     double max_stem_elems;    /* largest stem tensor, entries */
     int64_t device_bytes;     /* device memory held by the plan */
+    int32_t n_passes_cbank;   /* fused passes that take their (2,2) branch
+                                 matrices from the constant bank (launches
+                                 with one batch item); each launch of one is
+                                 preceded by a one-block staging kernel and a
+                                 device-to-device copy */
+    int32_t pad_;
 } tn_plan_stats;
 
 /* One stem step as the plan runs it (features for cost models). */
@@ -129,6 +135,8 @@ typedef struct {
     int32_t k, n;             /* contracted / new bits: C[m,n] = sum_k S[m,k] B[k,n] */
     int32_t pass;             /* fused pass index holding this step (-1: GEMM step) */
     int32_t gemm;             /* 1 if run as a tensor-core GEMM in fused mode */
+    int32_t pair;             /* 1 if its fused pass takes the rest indices in
+                                 adjacent pairs (16-byte shared-memory accesses) */
 } tn_step_info;
 
 /* Sec. 2-3: build the network of circuit c with the listed open qubits and the

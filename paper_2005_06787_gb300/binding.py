@@ -66,12 +66,13 @@ class tn_plan_stats(C.Structure):
                 ("n_passes_fused", C.c_int32), ("n_gemm_steps", C.c_int32),
                 ("n_open", C.c_int32), ("n_prefixes", C.c_int32), ("batch_items", C.c_int32),
                 ("stem_bytes_plain", C.c_double), ("stem_bytes_fused", C.c_double),
-                ("max_stem_elems", C.c_double), ("device_bytes", C.c_int64)]
+                ("max_stem_elems", C.c_double), ("device_bytes", C.c_int64),
+                ("n_passes_cbank", C.c_int32), ("pad_", C.c_int32)]
 
 
 class tn_step_info(C.Structure):
     _fields_ = [("r_in", C.c_int32), ("r_out", C.c_int32), ("k", C.c_int32), ("n", C.c_int32),
-                ("pass_", C.c_int32), ("gemm", C.c_int32)]
+                ("pass_", C.c_int32), ("gemm", C.c_int32), ("pair", C.c_int32)]
 
 
 class tn_launch_record(C.Structure):
@@ -325,7 +326,7 @@ def tn_plan_steps(plan: Plan):
     arr = (tn_step_info * max(n.value, 1))()
     w = C.c_int32()
     _check(L.tn_plan_steps(plan.handle, arr, n.value, C.byref(w)))
-    return [dict(r_in=a.r_in, r_out=a.r_out, k=a.k, n=a.n, pass_=a.pass_, gemm=a.gemm)
+    return [dict(r_in=a.r_in, r_out=a.r_out, k=a.k, n=a.n, pass_=a.pass_, gemm=a.gemm, pair=a.pair)
             for a in arr[:w.value]]
 
 

@@ -161,6 +161,11 @@ tn_status tn_plan_info(const tn_plan *plan, tn_plan_stats *out) {
         out->stem_bytes_fused = p.sp.bytes_fused;
         out->max_stem_elems = std::exp2((double)p.sp.max_rank);
         out->device_bytes = p.device_bytes;
+        out->n_passes_cbank = 0;
+        if (out->batch_items == 1)
+            for (auto &it : p.sp.fused_items)
+                if (it.kind == 0 && tn::pass_has_22_steps(p.sp.fused_passes[(size_t)it.pass]))
+                    ++out->n_passes_cbank;
     });
 }
 
@@ -195,6 +200,14 @@ tn_status tn_plan_steps(const tn_plan *plan, tn_step_info *out, int32_t max_step
             out[i].n = es.n;
             out[i].pass = p.sp.step_pass.empty() ? -1 : p.sp.step_pass[(size_t)i];
             out[i].gemm = p.sp.step_gemm.empty() ? 0 : p.sp.step_gemm[(size_t)i];
+            out[i].pair = 0;
+            if (out[i].pass >= 0 && !out[i].gemm) {
+                // a pass holds a run of consecutive steps, in slot order
+                int slot = 0;
+                while (i - slot - 1 >= 0 && p.sp.step_pass[(size_t)(i - slot - 1)] == out[i].pass) ++slot;
+                const tn::DevPass &P = p.sp.fused_passes[(size_t)out[i].pass];
+                if (slot < P.n_steps) out[i].pair = P.steps[slot].pair;
+            }
             ++w;
         }
         if (n_written) *n_written = out ? w : L;

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <memory>
 
 #include "plan.h"
 
@@ -393,6 +394,7 @@ void plan_contract(Plan &p, uint64_t s0, uint64_t s1, tn_precision prec, tn_exec
                 TN_CUDA(e);
                 it = p.graphs.emplace((int)prec, ge).first;
             }
+            ConstBankOrder order(st);
             for (uint64_t b = 0; b < nbatch; ++b) TN_CUDA(cudaGraphLaunch(it->second, st));
         }
     }
@@ -440,6 +442,8 @@ std::vector<tn_launch_record> plan_profile(Plan &p, uint64_t s0, tn_precision pr
     const int items_fused = p.SB * p.n_prefix;
     const int items = mode == TN_EXEC_FUSED ? (int)std::min<uint64_t>(s1 - s0, sb) * p.n_prefix
                                             : 1;
+    std::unique_ptr<ConstBankOrder> order;
+    if (mode == TN_EXEC_FUSED) order.reset(new ConstBankOrder(st));
     mark();
     if (mode == TN_EXEC_FUSED) {
         BatchArgs ba{p.d_state, p.SB, items_fused, 0};
@@ -532,6 +536,7 @@ std::vector<tn_launch_record> plan_profile(Plan &p, uint64_t s0, tn_precision pr
             cur = out;
         }
     }
+    order.reset();
     TN_CUDA(cudaStreamSynchronize(st));
     for (size_t i = 0; i < recs.size(); ++i) {
         float ms = 0;

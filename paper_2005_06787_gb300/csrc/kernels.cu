@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstddef>
 #include <cstdint>
+#include <mutex>
 
 #include "kernels.h"
 
@@ -157,6 +158,111 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 constexpr int PASS_THREADS = 256;
 constexpr size_t PASS_HEAD_BYTES = (offsetof(DevPass, steps) + 15) / 16 * 16;
 
+// Branch matrices of (2,2) steps in the constant bank. All units of a launch
+// with one batch item (one prefix, one slice) use the same branch matrices,
+// so the pass can take them as constant-bank operands of its FMAs at fixed
+// offsets: this frees the 32 registers a 4 x 4 complex matrix would hold and
+// the shared-memory loads that fill them at every step. stage_bm_kernel
+// gathers the matrices of the launch's slice into g_bm_stage, and a
+// device-to-device copy on the same stream moves them into c_bm right before
+// the pass; ConstBankOrder keeps calls on different streams from overlapping.
+constexpr int CB_ENTRIES = MAX_PASS_STEPS * 16;
+__constant__ float2 c_bm[CB_ENTRIES];
+__device__ float2 g_bm_stage[CB_ENTRIES];
+constexpr int CB_MAX_DEV = 64;
+static float2 *g_bm_stage_dev[CB_MAX_DEV];
+static cudaEvent_t g_cb_event[CB_MAX_DEV];
+static std::recursive_mutex g_cb_mutex;
+
+// one block: entries of every (2,2) step's branch matrix for batch item 0,
+// at 16 * (step slot) in the stage
+__global__ void stage_bm_kernel(const DevPass *__restrict__ gpass, const DevBranch *__restrict__ branches,
+                                const float2 *__restrict__ pool, BatchArgs ba) {
+    const int p = ba.p0;
+    const int64_t s = ba.state->slice_base;
+    const int n = gpass->n_steps;
+    for (int t = 0; t < n; ++t) {
+        const DevStep &S = gpass->steps[t];
+        if (S.branch < 0 || S.k != 2 || S.n != 2) continue;
+        const float2 *src = pool + branch_offset(branches[S.branch], p, s);
+        for (int i = threadIdx.x; i < 16; i += blockDim.x) g_bm_stage[t * 16 + i] = src[i];
+    }
+}
+
+// A (2,2) step in step slot T with its branch matrix in c_bm (k == n, so the
+// results go back to the kappa offsets); PAIR as in step_body_pair.
+template <int T, bool PAIR>
+__device__ __forceinline__ void step22_const(float2 *tile, const DevStep &S, int nt) {
+    int koff[4];
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) koff[kk] = S.koff[kk];
+    if (PAIR) {
+        const int npair = 1 << (S.rest - 1);
+        const int t_lo = S.lo[(2 * threadIdx.x) & 63];
+        for (int r2 = threadIdx.x; r2 < npair; r2 += nt) {
+            const int t = t_lo ^ S.hi[r2 >> 5];
+            float4 x[4];
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) x[kk] = *reinterpret_cast<const float4 *>(tile + (t ^ koff[kk]));
+#pragma unroll
+            for (int nn = 0; nn < 4; ++nn) {
+                float2 a0 = make_float2(0.f, 0.f), a1 = a0;
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    const float2 b = c_bm[T * 16 + kk * 4 + nn];
+                    cfma(a0, make_float2(x[kk].x, x[kk].y), b);
+                    cfma(a1, make_float2(x[kk].z, x[kk].w), b);
+                }
+                *reinterpret_cast<float4 *>(tile + (t ^ koff[nn])) = make_float4(a0.x, a0.y, a1.x, a1.y);
+            }
+        }
+    } else {
+        const int nrest = 1 << S.rest;
+        const int t_lo = S.lo[threadIdx.x & 63];
+        for (int r = threadIdx.x; r < nrest; r += nt) {
+            const int t = t_lo ^ S.hi[r >> 6];
+            float2 x[4];
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) x[kk] = tile[t ^ koff[kk]];
+#pragma unroll
+            for (int nn = 0; nn < 4; ++nn) {
+                float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) cfma(acc, x[kk], c_bm[T * 16 + kk * 4 + nn]);
+                tile[t ^ koff[nn]] = acc;
+            }
+        }
+    }
+}
+
+// other step shapes on the constant-bank path: one out-of-line copy of the
+// generic dispatch instead of one per step slot
+__device__ __noinline__ void run_step_outline(float2 *tile, const DevStep &S, const float2 *Bm, int nt) {
+    run_step(tile, S, Bm, nt);
+}
+
+// the steps of a pass, slot by slot from T (slots known at compile time)
+template <int T>
+__device__ __forceinline__ void run_steps_const(float2 *tile, const DevPass &P, const float2 *bm,
+                                                const int *bm_off, int nt) {
+    if constexpr (T < MAX_PASS_STEPS) {
+        if (T >= P.n_steps) return;
+        const DevStep &S = P.steps[T];
+        if (S.branch >= 0) {
+            if (S.k == 2 && S.n == 2) {
+                if (S.pair)
+                    step22_const<T, true>(tile, S, nt);
+                else
+                    step22_const<T, false>(tile, S, nt);
+            } else {
+                run_step_outline(tile, S, bm + bm_off[T], nt);
+            }
+            __syncthreads();
+        }
+        run_steps_const<T + 1>(tile, P, bm, bm_off, nt);
+    }
+}
+
 // A fused pass over batch items x tiles. Each block walks its tiles with two
 // tile buffers: while the steps run in place on one tile, the next tile's
 // entries stream into the other buffer with cp.async, so the HBM read of
@@ -164,12 +270,13 @@ constexpr size_t PASS_HEAD_BYTES = (offsetof(DevPass, steps) + 15) / 16 * 16;
 // edge i at tile position i; the store reads the final positions through the
 // st_lo / st_hi tables and writes the next layout.
 // Shared memory: pass header and used step tables | chunk tables | two tiles
-// | branch matrices of the current batch item.
+// | branch matrices of the current batch item. With cbank set (one batch item
+// per launch) (2,2) steps read their branch matrices from c_bm instead.
 template <int MINB>
 __global__ void __launch_bounds__(PASS_THREADS, MINB)
 pass_kernel(const DevPass *__restrict__ gpass, const int *__restrict__ chunks,
             const DevBranch *__restrict__ branches, const float2 *__restrict__ pool,
-            const float2 *__restrict__ in, float2 *__restrict__ out, BatchArgs ba) {
+            const float2 *__restrict__ in, float2 *__restrict__ out, BatchArgs ba, int cbank) {
     extern __shared__ __align__(16) unsigned char smem[];
     DevPass &P = *reinterpret_cast<DevPass *>(smem);
     const int n_steps_g = gpass->n_steps;
@@ -280,10 +387,14 @@ pass_kernel(const DevPass *__restrict__ gpass, const int *__restrict__ chunks,
         __syncthreads();
         if (valid) {
             float2 *tile = tbuf + buf * tile_max;
-            for (int t = 0; t < P.n_steps; ++t) {
-                if (P.steps[t].branch < 0) continue;
-                run_step(tile, P.steps[t], bm + bm_off[t], PASS_THREADS);
-                __syncthreads();
+            if (cbank) {
+                run_steps_const<0>(tile, P, bm, bm_off, PASS_THREADS);
+            } else {
+                for (int t = 0; t < P.n_steps; ++t) {
+                    if (P.steps[t].branch < 0) continue;
+                    run_step(tile, P.steps[t], bm + bm_off[t], PASS_THREADS);
+                    __syncthreads();
+                }
             }
             const unsigned tl = (unsigned)(u & (P.n_tiles - 1));
             const unsigned ob = __reduce_or_sync(0xffffffffu, ((tl >> lane) & 1u) ? my_fout : 0u);
@@ -302,6 +413,34 @@ pass_kernel(const DevPass *__restrict__ gpass, const int *__restrict__ chunks,
         __syncthreads();
     }
     cp_async_wait_all();
+}
+
+bool pass_uses_const_bank(const DevPass &h_pass, const BatchArgs &ba) {
+    if (ba.n_items != 1) return false;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= CB_MAX_DEV) return false;
+    {
+        std::lock_guard<std::recursive_mutex> lk(g_cb_mutex);
+        if (!g_bm_stage_dev[dev]) return false;
+    }
+    return pass_has_22_steps(h_pass);
+}
+
+ConstBankOrder::ConstBankOrder(cudaStream_t st) : st_(st) {
+    g_cb_mutex.lock();
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    int dev = 0;
+    if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone &&
+        cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < CB_MAX_DEV && g_cb_event[dev]) {
+        ev_ = g_cb_event[dev];
+        if (cudaStreamWaitEvent(st, ev_, 0) != cudaSuccess) ev_ = nullptr;
+    }
+    cudaGetLastError();
+}
+
+ConstBankOrder::~ConstBankOrder() {
+    if (ev_) cudaEventRecord(ev_, st_);
+    g_cb_mutex.unlock();
 }
 
 static size_t pass_smem_bytes(const DevPass &P) {
@@ -338,13 +477,23 @@ cudaError_t launch_pass(const DevPass *d_pass, const DevPass &h_pass, const int 
     }
     if (occ < 1) return cudaErrorInvalidConfiguration;
     const int64_t units = (int64_t)ba.n_items * h_pass.n_tiles;
+    const int cbank = pass_uses_const_bank(h_pass, ba) ? 1 : 0;
+    if (cbank) {
+        int dev = 0;
+        e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        stage_bm_kernel<<<1, 64, 0, st>>>(d_pass, d_branches, pool, ba);
+        e = cudaMemcpyToSymbolAsync(c_bm, g_bm_stage_dev[dev], sizeof(float2) * CB_ENTRIES, 0,
+                                    cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return e;
+    }
     const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(units, (int64_t)num_sms * occ));
     if (small_tile)
         pass_kernel<3><<<(unsigned)grid, PASS_THREADS, smem, st>>>(d_pass, d_chunks, d_branches, pool,
-                                                                   in, out, ba);
+                                                                   in, out, ba, cbank);
     else
         pass_kernel<2><<<(unsigned)grid, PASS_THREADS, smem, st>>>(d_pass, d_chunks, d_branches, pool,
-                                                                   in, out, ba);
+                                                                   in, out, ba, cbank);
     return cudaGetLastError();
 }
 
@@ -708,6 +857,24 @@ cudaError_t init_kernels() {
     if (e != cudaSuccess) return e;
     e = tc_gemm_init();
     if (e != cudaSuccess) return e;
+    {
+        // per device: the stage buffer's address and the event that orders
+        // users of the constant-bank copy
+        int dev = 0;
+        e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        std::lock_guard<std::recursive_mutex> lk(g_cb_mutex);
+        if (dev >= 0 && dev < CB_MAX_DEV && !g_bm_stage_dev[dev]) {
+            if (!g_cb_event[dev]) {
+                e = cudaEventCreateWithFlags(&g_cb_event[dev], cudaEventDisableTiming);
+                if (e != cudaSuccess) return e;
+            }
+            void *a = nullptr;
+            e = cudaGetSymbolAddress(&a, g_bm_stage);
+            if (e != cudaSuccess) return e;
+            g_bm_stage_dev[dev] = static_cast<float2 *>(a);
+        }
+    }
     return cudaFuncSetAttribute(cgemm_simt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 96 * 1024);
 }

@@ -31,6 +31,33 @@ struct SmallContract {
 };
 
 cudaError_t init_kernels();
+
+// A fused pass launched with one batch item reads the branch matrices of its
+// (2,2) steps from a per-device constant-bank copy that launch_pass stages on
+// the launch's stream (one gather kernel and one device-to-device copy).
+bool pass_uses_const_bank(const DevPass &h_pass, const BatchArgs &ba);
+inline bool pass_has_22_steps(const DevPass &h_pass) {
+    for (int t = 0; t < h_pass.n_steps; ++t)
+        if (h_pass.steps[t].branch >= 0 && h_pass.steps[t].k == 2 && h_pass.steps[t].n == 2) return true;
+    return false;
+}
+
+// Orders the calls that enqueue such passes: the constructor takes a
+// process-wide lock and makes `st` wait for the last call enqueued on this
+// device; the destructor records this call's end on `st` and unlocks. A
+// stream under capture is left alone (the graph is ordered where it is
+// launched).
+class ConstBankOrder {
+  public:
+    explicit ConstBankOrder(cudaStream_t st);
+    ~ConstBankOrder();
+    ConstBankOrder(const ConstBankOrder &) = delete;
+    ConstBankOrder &operator=(const ConstBankOrder &) = delete;
+
+  private:
+    cudaStream_t st_;
+    cudaEvent_t ev_ = nullptr;
+};
 cudaError_t launch_pass(const DevPass *d_pass, const DevPass &h_pass, const int *d_chunks,
                         const DevBranch *d_branches, const DevBranch *h_branches,
                         const float2 *pool, const float2 *in, float2 *out, BatchArgs ba,

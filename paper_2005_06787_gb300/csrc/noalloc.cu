@@ -101,6 +101,7 @@ void plan_contract_noalloc(Plan &p, uint64_t s0, uint64_t s1, cudaStream_t st, d
     const int items = (int)SB * p.n_prefix;
     BatchArgs ba{&S->state, (int)SB, items, 0};
     const uint64_t nbatch = (s1 - s0 + (uint64_t)SB - 1) / (uint64_t)SB;
+    ConstBankOrder order(st);
     for (uint64_t b = 0; b < nbatch; ++b) {
         int cur = -1;
         for (const FusedItem &it : p.sp.fused_items) {
