@@ -190,15 +190,19 @@ __global__ void stage_bm_kernel(const DevPass *__restrict__ gpass, const DevBran
 }
 
 // A (2,2) step in step slot T with its branch matrix in c_bm (k == n, so the
-// results go back to the kappa offsets); PAIR as in step_body_pair.
+// results go back to the kappa offsets); PAIR as in step_body_pair. S is the
+// step's descriptor in the kernel's parameter bank: its offsets and counts
+// are constant-bank operands, and its hi table is read at warp-uniform
+// indices. The lo table, which every lane reads at its own index, comes from
+// the shared-memory copy (divergent constant-bank reads serialise).
 template <int T, bool PAIR>
-__device__ __forceinline__ void step22_const(float2 *tile, const DevStep &S, int nt) {
+__device__ __forceinline__ void step22_const(float2 *tile, const DevStep &S, const int *lo_sm, int nt) {
     int koff[4];
 #pragma unroll
     for (int kk = 0; kk < 4; ++kk) koff[kk] = S.koff[kk];
     if (PAIR) {
         const int npair = 1 << (S.rest - 1);
-        const int t_lo = S.lo[(2 * threadIdx.x) & 63];
+        const int t_lo = lo_sm[(2 * threadIdx.x) & 63];
         for (int r2 = threadIdx.x; r2 < npair; r2 += nt) {
             const int t = t_lo ^ S.hi[r2 >> 5];
             float4 x[4];
@@ -218,7 +222,7 @@ __device__ __forceinline__ void step22_const(float2 *tile, const DevStep &S, int
         }
     } else {
         const int nrest = 1 << S.rest;
-        const int t_lo = S.lo[threadIdx.x & 63];
+        const int t_lo = lo_sm[threadIdx.x & 63];
         for (int r = threadIdx.x; r < nrest; r += nt) {
             const int t = t_lo ^ S.hi[r >> 6];
             float2 x[4];
@@ -241,25 +245,27 @@ __device__ __noinline__ void run_step_outline(float2 *tile, const DevStep &S, co
     run_step(tile, S, Bm, nt);
 }
 
-// the steps of a pass, slot by slot from T (slots known at compile time)
+// the steps of a pass, slot by slot from T (slots known at compile time); P is
+// the descriptor's shared-memory copy, CP the same descriptor passed by value
+// in the kernel's parameter bank
 template <int T>
-__device__ __forceinline__ void run_steps_const(float2 *tile, const DevPass &P, const float2 *bm,
-                                                const int *bm_off, int nt) {
+__device__ __forceinline__ void run_steps_const(float2 *tile, const DevPass &P, const DevPass &CP,
+                                                const float2 *bm, const int *bm_off, int nt) {
     if constexpr (T < MAX_PASS_STEPS) {
-        if (T >= P.n_steps) return;
-        const DevStep &S = P.steps[T];
+        if (T >= CP.n_steps) return;
+        const DevStep &S = CP.steps[T];
         if (S.branch >= 0) {
             if (S.k == 2 && S.n == 2) {
                 if (S.pair)
-                    step22_const<T, true>(tile, S, nt);
+                    step22_const<T, true>(tile, S, P.steps[T].lo, nt);
                 else
-                    step22_const<T, false>(tile, S, nt);
+                    step22_const<T, false>(tile, S, P.steps[T].lo, nt);
             } else {
-                run_step_outline(tile, S, bm + bm_off[T], nt);
+                run_step_outline(tile, P.steps[T], bm + bm_off[T], nt);
             }
             __syncthreads();
         }
-        run_steps_const<T + 1>(tile, P, bm, bm_off, nt);
+        run_steps_const<T + 1>(tile, P, CP, bm, bm_off, nt);
     }
 }
 
@@ -271,12 +277,14 @@ __device__ __forceinline__ void run_steps_const(float2 *tile, const DevPass &P, 
 // st_lo / st_hi tables and writes the next layout.
 // Shared memory: pass header and used step tables | chunk tables | two tiles
 // | branch matrices of the current batch item. With cbank set (one batch item
-// per launch) (2,2) steps read their branch matrices from c_bm instead.
+// per launch) (2,2) steps read their branch matrices from c_bm and their
+// descriptors from cpass, the pass descriptor passed by value.
 template <int MINB>
 __global__ void __launch_bounds__(PASS_THREADS, MINB)
 pass_kernel(const DevPass *__restrict__ gpass, const int *__restrict__ chunks,
             const DevBranch *__restrict__ branches, const float2 *__restrict__ pool,
-            const float2 *__restrict__ in, float2 *__restrict__ out, BatchArgs ba, int cbank) {
+            const float2 *__restrict__ in, float2 *__restrict__ out, BatchArgs ba, int cbank,
+            const __grid_constant__ DevPass cpass) {
     extern __shared__ __align__(16) unsigned char smem[];
     DevPass &P = *reinterpret_cast<DevPass *>(smem);
     const int n_steps_g = gpass->n_steps;
@@ -388,7 +396,7 @@ pass_kernel(const DevPass *__restrict__ gpass, const int *__restrict__ chunks,
         if (valid) {
             float2 *tile = tbuf + buf * tile_max;
             if (cbank) {
-                run_steps_const<0>(tile, P, bm, bm_off, PASS_THREADS);
+                run_steps_const<0>(tile, P, cpass, bm, bm_off, PASS_THREADS);
             } else {
                 for (int t = 0; t < P.n_steps; ++t) {
                     if (P.steps[t].branch < 0) continue;
@@ -490,10 +498,10 @@ cudaError_t launch_pass(const DevPass *d_pass, const DevPass &h_pass, const int 
     const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(units, (int64_t)num_sms * occ));
     if (small_tile)
         pass_kernel<3><<<(unsigned)grid, PASS_THREADS, smem, st>>>(d_pass, d_chunks, d_branches, pool,
-                                                                   in, out, ba, cbank);
+                                                                   in, out, ba, cbank, h_pass);
     else
         pass_kernel<2><<<(unsigned)grid, PASS_THREADS, smem, st>>>(d_pass, d_chunks, d_branches, pool,
-                                                                   in, out, ba, cbank);
+                                                                   in, out, ba, cbank, h_pass);
     return cudaGetLastError();
 }
 
