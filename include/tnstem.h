@@ -121,9 +121,10 @@ typedef struct {
     double stem_bytes_fused;  /* algorithmic HBM bytes per slice, fused mode */
     double max_stem_elems;    /* largest stem tensor, entries */
     int64_t device_bytes;     /* device memory held by the plan */
-    int32_t n_passes_cbank;   /* fused passes that take their (2,2) branch
-                                 matrices from the constant bank (launches
-                                 with one batch item); each launch of one is
+    int32_t n_passes_cbank;   /* fused passes that take branch matrices from
+                                 the constant bank ((2,2) steps and paired
+                                 (2,1), (1,3), (1,2) steps, in launches with
+                                 one batch item); each launch of one is
                                  preceded by a one-block staging kernel and a
                                  device-to-device copy */
     int32_t pad_;

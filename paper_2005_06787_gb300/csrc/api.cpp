@@ -164,7 +164,7 @@ tn_status tn_plan_info(const tn_plan *plan, tn_plan_stats *out) {
         out->n_passes_cbank = 0;
         if (out->batch_items == 1)
             for (auto &it : p.sp.fused_items)
-                if (it.kind == 0 && tn::pass_has_22_steps(p.sp.fused_passes[(size_t)it.pass]))
+                if (it.kind == 0 && tn::pass_has_const_steps(p.sp.fused_passes[(size_t)it.pass]))
                     ++out->n_passes_cbank;
     });
 }

@@ -158,24 +158,51 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 constexpr int PASS_THREADS = 256;
 constexpr size_t PASS_HEAD_BYTES = (offsetof(DevPass, steps) + 15) / 16 * 16;
 
-// Branch matrices of (2,2) steps in the constant bank. All units of a launch
-// with one batch item (one prefix, one slice) use the same branch matrices,
-// so the pass can take them as constant-bank operands of its FMAs at fixed
-// offsets: this frees the 32 registers a 4 x 4 complex matrix would hold and
-// the shared-memory loads that fill them at every step. stage_bm_kernel
+// Branch matrices in the constant bank. All units of a launch with one batch
+// item (one prefix, one slice) use the same branch matrices, so the pass can
+// take them as constant-bank operands of its FMAs at fixed offsets: for a
+// (2,2) step this frees the 32 registers a 4 x 4 complex matrix would hold
+// and the shared-memory loads that fill them at every step. stage_bm_kernel
 // gathers the matrices of the launch's slice into g_bm_stage, and a
 // device-to-device copy on the same stream moves them into c_bm right before
 // the pass; ConstBankOrder keeps calls on different streams from overlapping.
 constexpr int CB_ENTRIES = MAX_PASS_STEPS * 16;
 __constant__ float2 c_bm[CB_ENTRIES];
 __device__ float2 g_bm_stage[CB_ENTRIES];
+// the same entries as (Br, Bi, -Bi, Br) for the packed FP32 FMAs of paired
+// (2,2) steps
+__constant__ float4 c_bm2[CB_ENTRIES];
+__device__ float4 g_bm2_stage[CB_ENTRIES];
+
+// Packed FP32 pairs (fma.rn.f32x2): one instruction does two FP32 FMAs at
+// the same lane rate as two FFMA, which halves the issue slots of the
+// arithmetic in an issue-bound loop.
+__device__ __forceinline__ unsigned long long pk2(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1,%2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float2 upk2(unsigned long long x) {
+    float lo, hi;
+    asm("mov.b64 {%0,%1}, %2;" : "=f"(lo), "=f"(hi) : "l"(x));
+    return make_float2(lo, hi);
+}
+__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b,
+                                                    unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
 constexpr int CB_MAX_DEV = 64;
 static float2 *g_bm_stage_dev[CB_MAX_DEV];
+static float4 *g_bm2_stage_dev[CB_MAX_DEV];
 static cudaEvent_t g_cb_event[CB_MAX_DEV];
 static std::recursive_mutex g_cb_mutex;
 
-// one block: entries of every (2,2) step's branch matrix for batch item 0,
-// at 16 * (step slot) in the stage
+// one block: entries of every step's branch matrix (at most 16) for batch
+// item 0, at 16 * (step slot) in the stage, and each entry's expansion for
+// the packed FMAs
 __global__ void stage_bm_kernel(const DevPass *__restrict__ gpass, const DevBranch *__restrict__ branches,
                                 const float2 *__restrict__ pool, BatchArgs ba) {
     const int p = ba.p0;
@@ -183,14 +210,20 @@ __global__ void stage_bm_kernel(const DevPass *__restrict__ gpass, const DevBran
     const int n = gpass->n_steps;
     for (int t = 0; t < n; ++t) {
         const DevStep &S = gpass->steps[t];
-        if (S.branch < 0 || S.k != 2 || S.n != 2) continue;
+        if (S.branch < 0) continue;
         const float2 *src = pool + branch_offset(branches[S.branch], p, s);
-        for (int i = threadIdx.x; i < 16; i += blockDim.x) g_bm_stage[t * 16 + i] = src[i];
+        const int cnt = 1 << (S.k + S.n);
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+            const float2 b = src[i];
+            g_bm_stage[t * 16 + i] = b;
+            g_bm2_stage[t * 16 + i] = make_float4(b.x, b.y, -b.y, b.x);
+        }
     }
 }
 
-// A (2,2) step in step slot T with its branch matrix in c_bm (k == n, so the
-// results go back to the kappa offsets); PAIR as in step_body_pair. S is the
+// A (2,2) step in step slot T with its branch matrix in c_bm (c_bm2 for the
+// packed FMAs of the paired form; k == n, so the results go back to the kappa
+// offsets); PAIR as in step_body_pair. S is the
 // step's descriptor in the kernel's parameter bank: its offsets and counts
 // are constant-bank operands, and its hi table is read at warp-uniform
 // indices. The lo table, which every lane reads at its own index, comes from
@@ -208,16 +241,30 @@ __device__ __forceinline__ void step22_const(float2 *tile, const DevStep &S, con
             float4 x[4];
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) x[kk] = *reinterpret_cast<const float4 *>(tile + (t ^ koff[kk]));
+            // (acc.re, acc.im) += (x.re, x.re) * (Br, Bi) + (x.im, x.im) * (-Bi, Br):
+            // the FMAs of cfma in the same order, two per instruction
+            unsigned long long X0[4], S0[4], X1[4], S1[4];
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                X0[kk] = pk2(x[kk].x, x[kk].x);
+                S0[kk] = pk2(x[kk].y, x[kk].y);
+                X1[kk] = pk2(x[kk].z, x[kk].z);
+                S1[kk] = pk2(x[kk].w, x[kk].w);
+            }
 #pragma unroll
             for (int nn = 0; nn < 4; ++nn) {
-                float2 a0 = make_float2(0.f, 0.f), a1 = a0;
+                unsigned long long a0 = 0ull, a1 = 0ull;
 #pragma unroll
                 for (int kk = 0; kk < 4; ++kk) {
-                    const float2 b = c_bm[T * 16 + kk * 4 + nn];
-                    cfma(a0, make_float2(x[kk].x, x[kk].y), b);
-                    cfma(a1, make_float2(x[kk].z, x[kk].w), b);
+                    const float4 b = c_bm2[T * 16 + kk * 4 + nn];
+                    const unsigned long long b1 = pk2(b.x, b.y), b2 = pk2(b.z, b.w);
+                    a0 = ffma2(X0[kk], b1, a0);
+                    a0 = ffma2(S0[kk], b2, a0);
+                    a1 = ffma2(X1[kk], b1, a1);
+                    a1 = ffma2(S1[kk], b2, a1);
                 }
-                *reinterpret_cast<float4 *>(tile + (t ^ koff[nn])) = make_float4(a0.x, a0.y, a1.x, a1.y);
+                const float2 y0 = upk2(a0), y1 = upk2(a1);
+                *reinterpret_cast<float4 *>(tile + (t ^ koff[nn])) = make_float4(y0.x, y0.y, y1.x, y1.y);
             }
         }
     } else {
@@ -235,6 +282,37 @@ __device__ __forceinline__ void step22_const(float2 *tile, const DevStep &S, con
                 for (int kk = 0; kk < 4; ++kk) cfma(acc, x[kk], c_bm[T * 16 + kk * 4 + nn]);
                 tile[t ^ koff[nn]] = acc;
             }
+        }
+    }
+}
+
+// a paired step of shape (K, N) in slot T with its branch matrix in c_bm:
+// (2,1), (1,3) and (1,2), the other shapes the 53-qubit stems use most
+template <int T, int K, int N>
+__device__ __forceinline__ void stepkn_const_pair(float2 *tile, const DevStep &S, const int *lo_sm, int nt) {
+    constexpr int NK = 1 << K, NN = 1 << N;
+    int koff[NK], noff[NN];
+#pragma unroll
+    for (int kk = 0; kk < NK; ++kk) koff[kk] = S.koff[kk];
+#pragma unroll
+    for (int nn = 0; nn < NN; ++nn) noff[nn] = (K == N) ? koff[nn % NK] : S.noff[nn];
+    const int npair = 1 << (S.rest - 1);
+    const int t_lo = lo_sm[(2 * threadIdx.x) & 63];
+    for (int r2 = threadIdx.x; r2 < npair; r2 += nt) {
+        const int t = t_lo ^ S.hi[r2 >> 5];
+        float4 x[NK];
+#pragma unroll
+        for (int kk = 0; kk < NK; ++kk) x[kk] = *reinterpret_cast<const float4 *>(tile + (t ^ koff[kk]));
+#pragma unroll
+        for (int nn = 0; nn < NN; ++nn) {
+            float2 a0 = make_float2(0.f, 0.f), a1 = a0;
+#pragma unroll
+            for (int kk = 0; kk < NK; ++kk) {
+                const float2 b = c_bm[T * 16 + kk * NN + nn];
+                cfma(a0, make_float2(x[kk].x, x[kk].y), b);
+                cfma(a1, make_float2(x[kk].z, x[kk].w), b);
+            }
+            *reinterpret_cast<float4 *>(tile + (t ^ noff[nn])) = make_float4(a0.x, a0.y, a1.x, a1.y);
         }
     }
 }
@@ -260,6 +338,12 @@ __device__ __forceinline__ void run_steps_const(float2 *tile, const DevPass &P, 
                     step22_const<T, true>(tile, S, P.steps[T].lo, nt);
                 else
                     step22_const<T, false>(tile, S, P.steps[T].lo, nt);
+            } else if (S.pair && S.k == 2 && S.n == 1) {
+                stepkn_const_pair<T, 2, 1>(tile, S, P.steps[T].lo, nt);
+            } else if (S.pair && S.k == 1 && S.n == 3) {
+                stepkn_const_pair<T, 1, 3>(tile, S, P.steps[T].lo, nt);
+            } else if (S.pair && S.k == 1 && S.n == 2) {
+                stepkn_const_pair<T, 1, 2>(tile, S, P.steps[T].lo, nt);
             } else {
                 run_step_outline(tile, P.steps[T], bm + bm_off[T], nt);
             }
@@ -276,14 +360,16 @@ __device__ __forceinline__ void run_steps_const(float2 *tile, const DevPass &P, 
 // edge i at tile position i; the store reads the final positions through the
 // st_lo / st_hi tables and writes the next layout.
 // Shared memory: pass header and used step tables | chunk tables | two tiles
-// | branch matrices of the current batch item. With cbank set (one batch item
-// per launch) (2,2) steps read their branch matrices from c_bm and their
-// descriptors from cpass, the pass descriptor passed by value.
-template <int MINB>
+// | branch matrices of the current batch item. The CBANK instantiation (one
+// batch item per launch) reads the branch matrices of its (2,2) and paired
+// (2,1), (1,3), (1,2) steps from the constant bank and their descriptors from
+// cpass, the pass descriptor passed by value; the two instantiations get
+// their registers allocated separately.
+template <int MINB, bool CBANK>
 __global__ void __launch_bounds__(PASS_THREADS, MINB)
 pass_kernel(const DevPass *__restrict__ gpass, const int *__restrict__ chunks,
             const DevBranch *__restrict__ branches, const float2 *__restrict__ pool,
-            const float2 *__restrict__ in, float2 *__restrict__ out, BatchArgs ba, int cbank,
+            const float2 *__restrict__ in, float2 *__restrict__ out, BatchArgs ba,
             const __grid_constant__ DevPass cpass) {
     extern __shared__ __align__(16) unsigned char smem[];
     DevPass &P = *reinterpret_cast<DevPass *>(smem);
@@ -362,8 +448,10 @@ pass_kernel(const DevPass *__restrict__ gpass, const int *__restrict__ chunks,
             // each j adds one block-uniform term
             if (ld_i0 < tin_n) {
                 const float2 *s0 = src + ld_off0;
-                for (int j = 0, idx = ld_i0; idx < tin_n; ++j, idx += 2 * PASS_THREADS)
-                    cp_async16(dstb + (ld_sw0 ^ dev_swizzle(j << 9)), s0 + cin_tab[(j << 9) >> c_in]);
+#pragma unroll
+                for (int j = 0; j < (1 << MAX_TILE_BITS) / (2 * PASS_THREADS); ++j)
+                    if ((j << 9) < tin_n)
+                        cp_async16(dstb + (ld_sw0 ^ dev_swizzle(j << 9)), s0 + cin_tab[(j << 9) >> c_in]);
             }
         } else {
             for (int idx = threadIdx.x; idx < tin_n; idx += PASS_THREADS)
@@ -395,7 +483,7 @@ pass_kernel(const DevPass *__restrict__ gpass, const int *__restrict__ chunks,
         __syncthreads();
         if (valid) {
             float2 *tile = tbuf + buf * tile_max;
-            if (cbank) {
+            if constexpr (CBANK) {
                 run_steps_const<0>(tile, P, cpass, bm, bm_off, PASS_THREADS);
             } else {
                 for (int t = 0; t < P.n_steps; ++t) {
@@ -410,9 +498,13 @@ pass_kernel(const DevPass *__restrict__ gpass, const int *__restrict__ chunks,
             if (st_pair) {
                 // output bit 0 is tile position 0: entry pairs move as 16 bytes
                 float2 *d0 = dst + st_off0;
-                for (int j = 0, idx = ld_i0; idx < tout_n; ++j, idx += 2 * PASS_THREADS)
-                    *reinterpret_cast<float4 *>(d0 + cout_tab[(j << 9) >> c_out]) =
-                        *reinterpret_cast<const float4 *>(tile + (st_t0 ^ P.st_hi[j << 3]));
+                if (ld_i0 < tout_n) {
+#pragma unroll
+                    for (int j = 0; j < (1 << MAX_TILE_BITS) / (2 * PASS_THREADS); ++j)
+                        if ((j << 9) < tout_n)
+                            *reinterpret_cast<float4 *>(d0 + cout_tab[(j << 9) >> c_out]) =
+                                *reinterpret_cast<const float4 *>(tile + (st_t0 ^ cpass.st_hi[j << 3]));
+                }
             } else {
                 for (int idx = threadIdx.x; idx < tout_n; idx += PASS_THREADS)
                     dst[cout_tab[idx >> c_out] + (idx & cout_mask)] = tile[st_lo ^ P.st_hi[idx >> 6]];
@@ -431,7 +523,7 @@ bool pass_uses_const_bank(const DevPass &h_pass, const BatchArgs &ba) {
         std::lock_guard<std::recursive_mutex> lk(g_cb_mutex);
         if (!g_bm_stage_dev[dev]) return false;
     }
-    return pass_has_22_steps(h_pass);
+    return pass_has_const_steps(h_pass);
 }
 
 ConstBankOrder::ConstBankOrder(cudaStream_t st) : st_(st) {
@@ -475,17 +567,19 @@ cudaError_t launch_pass(const DevPass *d_pass, const DevPass &h_pass, const int 
     // three blocks per SM (registers capped at 80) measured faster than two
     // blocks with 96 registers; the 96-register variant is used only when the
     // tile's shared memory does not fit three blocks
+    const bool cbank = pass_uses_const_bank(h_pass, ba);
+    auto k3 = cbank ? &pass_kernel<3, true> : &pass_kernel<3, false>;
+    auto k2 = cbank ? &pass_kernel<2, true> : &pass_kernel<2, false>;
     int occ = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pass_kernel<3>, PASS_THREADS, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k3, PASS_THREADS, smem);
     if (e != cudaSuccess) return e;
     const bool small_tile = occ >= 3;
     if (!small_tile) {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pass_kernel<2>, PASS_THREADS, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k2, PASS_THREADS, smem);
         if (e != cudaSuccess) return e;
     }
     if (occ < 1) return cudaErrorInvalidConfiguration;
     const int64_t units = (int64_t)ba.n_items * h_pass.n_tiles;
-    const int cbank = pass_uses_const_bank(h_pass, ba) ? 1 : 0;
     if (cbank) {
         int dev = 0;
         e = cudaGetDevice(&dev);
@@ -494,14 +588,13 @@ cudaError_t launch_pass(const DevPass *d_pass, const DevPass &h_pass, const int 
         e = cudaMemcpyToSymbolAsync(c_bm, g_bm_stage_dev[dev], sizeof(float2) * CB_ENTRIES, 0,
                                     cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) return e;
+        e = cudaMemcpyToSymbolAsync(c_bm2, g_bm2_stage_dev[dev], sizeof(float4) * CB_ENTRIES, 0,
+                                    cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return e;
     }
     const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(units, (int64_t)num_sms * occ));
-    if (small_tile)
-        pass_kernel<3><<<(unsigned)grid, PASS_THREADS, smem, st>>>(d_pass, d_chunks, d_branches, pool,
-                                                                   in, out, ba, cbank, h_pass);
-    else
-        pass_kernel<2><<<(unsigned)grid, PASS_THREADS, smem, st>>>(d_pass, d_chunks, d_branches, pool,
-                                                                   in, out, ba, cbank, h_pass);
+    (small_tile ? k3 : k2)<<<(unsigned)grid, PASS_THREADS, smem, st>>>(d_pass, d_chunks, d_branches, pool,
+                                                                       in, out, ba, h_pass);
     return cudaGetLastError();
 }
 
@@ -858,11 +951,11 @@ cudaError_t launch_permute(const float2 *in, float2 *out, int rank, const int *d
 
 // Raise the dynamic shared-memory limits once, outside any stream capture.
 cudaError_t init_kernels() {
-    cudaError_t e = cudaFuncSetAttribute(pass_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         200 * 1024);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(pass_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (e != cudaSuccess) return e;
+    cudaError_t e = cudaSuccess;
+    for (auto k : {&pass_kernel<2, false>, &pass_kernel<3, false>, &pass_kernel<2, true>, &pass_kernel<3, true>}) {
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e != cudaSuccess) return e;
+    }
     e = tc_gemm_init();
     if (e != cudaSuccess) return e;
     {
@@ -881,6 +974,9 @@ cudaError_t init_kernels() {
             e = cudaGetSymbolAddress(&a, g_bm_stage);
             if (e != cudaSuccess) return e;
             g_bm_stage_dev[dev] = static_cast<float2 *>(a);
+            e = cudaGetSymbolAddress(&a, g_bm2_stage);
+            if (e != cudaSuccess) return e;
+            g_bm2_stage_dev[dev] = static_cast<float4 *>(a);
         }
     }
     return cudaFuncSetAttribute(cgemm_simt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -33,14 +33,22 @@ struct SmallContract {
 cudaError_t init_kernels();
 
 // A fused pass launched with one batch item reads the branch matrices of its
-// (2,2) steps from a per-device constant-bank copy that launch_pass stages on
-// the launch's stream (one gather kernel and one device-to-device copy).
+// (2,2) steps and paired (2,1), (1,3), (1,2) steps from a per-device
+// constant-bank copy that launch_pass stages on the launch's stream (one
+// gather kernel and one device-to-device copy); other shapes keep them in
+// shared memory.
 bool pass_uses_const_bank(const DevPass &h_pass, const BatchArgs &ba);
-inline bool pass_has_22_steps(const DevPass &h_pass) {
+inline bool step_on_const_bank(const DevStep &S) {
+    if (S.branch < 0) return false;
+    if (S.k == 2 && S.n == 2) return true;
+    return S.pair && ((S.k == 2 && S.n == 1) || (S.k == 1 && S.n == 3) || (S.k == 1 && S.n == 2));
+}
+inline bool pass_has_const_steps(const DevPass &h_pass) {
     for (int t = 0; t < h_pass.n_steps; ++t)
-        if (h_pass.steps[t].branch >= 0 && h_pass.steps[t].k == 2 && h_pass.steps[t].n == 2) return true;
+        if (step_on_const_bank(h_pass.steps[t])) return true;
     return false;
 }
+
 
 // Orders the calls that enqueue such passes: the constructor takes a
 // process-wide lock and makes `st` wait for the last call enqueued on this

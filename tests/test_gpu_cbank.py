@@ -1,7 +1,7 @@
 """Branch matrices in the constant bank: a fused pass launched with one batch
-item (one prefix, one slice) takes the branch matrices of its (2,2) steps from
-a constant-bank copy staged on the launch's stream; launches with several
-items read them from shared memory. Both paths against the FP64 oracle
+item (one prefix, one slice) takes the branch matrices of its (2,2) steps and
+paired (2,1), (1,3), (1,2) steps from a constant-bank copy staged on the
+launch's stream; launches with several items read them from shared memory. Both paths against the FP64 oracle
 (relative L2 error <= 1e-5), against each other, per slice, and with two
 plans running on two streams at once.
 """
@@ -88,7 +88,11 @@ def test_constant_bank_and_shared_memory_paths_agree_per_slice():
     c, oq, cb, net, plan1 = _sliced_case(1)
     _, _, _, _, plan4 = _sliced_case(4)
     i1, i4 = P.tn_plan_info(plan1), P.tn_plan_info(plan4)
-    assert any(is_22(s, 1) for s in P.tn_plan_steps(plan1))
+    steps = P.tn_plan_steps(plan1)
+    assert any(is_22(s, 1) for s in steps) and any(is_22(s, 0) for s in steps)
+    # the other shapes taken from the constant bank when paired
+    paired = {(s["k"], s["n"]) for s in steps if s["pass_"] >= 0 and not s["gemm"] and s["pair"]}
+    assert {(2, 1), (1, 3), (1, 2)} <= paired
     # the same scheme (the planner is seeded); only the launch batching differs
     assert P.tn_plan_steps(plan1) == P.tn_plan_steps(plan4)
     assert i1["batch_items"] == 1 and i1["n_passes_cbank"] > 0
