@@ -400,11 +400,15 @@ def _closed_form(c, oq, closed_bits, sliced_by_wire, slice_id):
     return scal * out, scale
 
 
-@pytest.mark.parametrize("name,n_open", [("diag53_m14", None), ("diag53_m12", None),
-                                         ("diag53_m12", 0), ("diag53_m12", 4), ("diag53_m12", 8)])
-def test_full_size_plan_identity_fsim_closed_form(name, n_open):
+@pytest.mark.parametrize("name,n_open,extra", [("diag53_m14", None, {}),
+                                               ("diag53_m14", None, {"tile_bits": 12, "max_pass_steps": 8}),
+                                               ("diag53_m12", None, {}), ("diag53_m12", 0, {}),
+                                               ("diag53_m12", 4, {}), ("diag53_m12", 8, {})])
+def test_full_size_plan_identity_fsim_closed_form(name, n_open, extra):
     # the 53-qubit 12-cycle workload is also run at 1, 16 and 256 amplitudes
-    # per batch (0, 4, 8 open qubits) beside its 64-amplitude default
+    # per batch (0, 4, 8 open qubits) beside its 64-amplitude default; the
+    # 14-cycle one also with the tile and steps per pass its bench launch
+    # configuration uses (the learned search's pick)
     from bench import plan_options, workload_inputs
     cfg = CONFIGS[name]
     c, oq, cb_bench = workload_inputs(name)
@@ -415,7 +419,7 @@ def test_full_size_plan_identity_fsim_closed_form(name, n_open):
     closed = [q for q in range(c.n_qubits) if q not in set(oq)]
     v0 = _qubit_vectors(c0, {}, 0)
     cb = [int(np.argmax(np.abs(v0[q]))) for q in closed]
-    opts = plan_options(name)
+    opts = dict(plan_options(name), **extra)
     net_ref, plan_ref = _plan(c, oq, cb_bench, **opts)
     net, plan = _plan(c0, oq, cb, **opts)
     o1, s1 = P.tn_plan_export(plan_ref)
