@@ -102,6 +102,15 @@ typedef struct {
                                  annealed stems, the best by unsliced cost plus
                                  width excess (0 = all) */
     uint64_t seed;
+    int32_t start_cluster;    /* the first restart grows its stem from this branch
+                                 cluster (clusters are numbered for the seed's
+                                 random stream), without noise (default 0) */
+    int32_t stem_starts;      /* > 0: instead of the restarts, grow stems without
+                                 noise from this many start clusters spread
+                                 evenly over all clusters (every cluster when
+                                 there are fewer), each annealed, sliced and
+                                 refined on the host's threads; the cheapest
+                                 scheme wins, whatever the thread count (0 = off) */
 } tn_plan_opts;
 
 typedef struct {

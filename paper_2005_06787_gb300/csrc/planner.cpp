@@ -11,6 +11,10 @@
 // brute-forces the order of short windows of consecutive stem steps, the
 // branch-switch move of the paper's local-optimisation figure.
 #include <algorithm>
+#include <atomic>
+#include <exception>
+#include <mutex>
+#include <thread>
 #include <array>
 #include <cmath>
 #include <limits>
@@ -564,50 +568,102 @@ Scheme plan_scheme(const Network &net, const tn_plan_opts &o) {
     }
     // seeds: spread over clusters deterministically, the rest random
     std::uniform_int_distribution<int> pick(0, C - 1);
-    auto consider = [&](int seed, const std::vector<int> &order, const Bits &sliced,
-                        const std::vector<int> &sl) {
-        StemEval ev = eval_stem(B, seed, order, sliced);
-        if (ev.max_rank > limit) return false;
-        double sc = scheme_score(ev, (int)sl.size(), limit);
-        if (sc < best_score) {
-            best_score = sc;
-            best.clusters = clusters;
-            best.seed_cluster = seed;
-            best.stem_order = order;
-            best.sliced = sliced;
-            best.sliced_list = sl;
-        }
-        return true;
+    struct Candidate {
+        double score = INFINITY;
+        int seed = -1;
+        std::vector<int> order, sl;
+        Bits sliced;
+    };
+    auto take = [&](const Candidate &c) {
+        if (c.seed < 0 || !(c.score < best_score)) return;
+        best_score = c.score;
+        best.clusters = clusters;
+        best.seed_cluster = c.seed;
+        best.stem_order = c.order;
+        best.sliced = c.sliced;
+        best.sliced_list = c.sl;
     };
     // slicing and refinement of one annealed order: dynamic slicing with an
     // anneal after every pick, an order anneal that may not widen, the joint
     // order / sliced-set anneal, window optimisation. False when slicing
-    // misses the limit.
-    auto slice_refine = [&](int seed, std::vector<int> order, long ann) {
+    // misses the limit. Reads only shared inputs and the given random stream.
+    auto slice_refine_into = [&](int seed, std::vector<int> order, long ann, std::mt19937_64 &r,
+                                 Candidate &out) {
         Bits sliced(net.n_edges());
         std::vector<int> sl;
-        if (!dynamic_slice(net, B, seed, order, sliced, sl, limit, o.min_sliced, max_sl, lo_iters, ann / 10,
-                           rng))
+        if (!dynamic_slice(net, B, seed, order, sliced, sl, limit, o.min_sliced, max_sl, lo_iters, ann / 10, r))
             return false;
-        anneal_order(B, seed, order, sliced, limit, ann / 2, rng, 0.3, 0.01, 48, limit);
-        anneal_sliced(net, B, seed, order, sliced, sl, limit, o.min_sliced, ann / 4, rng);
+        anneal_order(B, seed, order, sliced, limit, ann / 2, r, 0.3, 0.01, 48, limit);
+        anneal_sliced(net, B, seed, order, sliced, sl, limit, o.min_sliced, ann / 4, r);
         local_opt_sweeps(B, seed, order, sliced, limit, lo_iters, (int)sl.size());
-        return consider(seed, order, sliced, sl);
+        StemEval ev = eval_stem(B, seed, order, sliced);
+        if (ev.max_rank > limit) return false;
+        out.score = scheme_score(ev, (int)sl.size(), limit);
+        out.seed = seed;
+        out.order = std::move(order);
+        out.sliced = sliced;
+        out.sl = std::move(sl);
+        return true;
+    };
+    auto slice_refine = [&](int seed, std::vector<int> order, long ann) {
+        Candidate c;
+        if (!slice_refine_into(seed, std::move(order), ann, rng, c)) return false;
+        take(c);
+        return true;
     };
     // unsliced anneal + window optimisation of a grown stem
-    auto shape = [&](int seed, std::vector<int> order, long ann) {
+    auto shape_with = [&](int seed, std::vector<int> order, long ann, std::mt19937_64 &r) {
         Bits none(net.n_edges());
-        anneal_order(B, seed, order, none, limit, ann, rng);
+        anneal_order(B, seed, order, none, limit, ann, r);
         local_opt_sweeps(B, seed, order, none, limit, lo_iters, 0);
         return order;
     };
-    if (o.slice_restarts <= 0 || o.slice_restarts >= restarts) {
+    auto shape = [&](int seed, std::vector<int> order, long ann) { return shape_with(seed, std::move(order), ann, rng); };
+    const int start0 = ((o.start_cluster % C) + C) % C;
+    if (o.stem_starts > 0) {
+        // stems grown without noise from stem_starts start clusters spread
+        // evenly over all clusters, each annealed, sliced and refined on its
+        // own random stream (seeded by the planner seed and its start), on the
+        // host's threads; the cheapest wins (ties: the earlier start), so the
+        // result does not depend on the thread count
+        const int n = std::min(o.stem_starts, C);
+        std::vector<int> starts;
+        for (int i = 0; i < n; ++i) starts.push_back((int)(((int64_t)i * C) / n));
+        std::vector<Candidate> res((size_t)n);
+        std::atomic<int> next{0};
+        std::exception_ptr err;
+        std::mutex err_mu;
+        auto worker = [&]() {
+            for (int i = next.fetch_add(1); i < n; i = next.fetch_add(1)) {
+                try {
+                    const int seed = starts[(size_t)i];
+                    std::mt19937_64 r((o.seed ? o.seed : 0x5eedull) ^
+                                      (0x9e3779b97f4a7c15ull * (uint64_t)(seed + 1)));
+                    const std::vector<int> grown = grow_stem(B, seed, r, 0.0);
+                    Candidate c;
+                    if (!slice_refine_into(seed, shape_with(seed, grown, anneal, r), anneal, r, c) && anneal > 0)
+                        slice_refine_into(seed, shape_with(seed, grown, 0, r), 0, r, c);
+                    res[(size_t)i] = std::move(c);
+                } catch (...) {
+                    std::lock_guard<std::mutex> lk(err_mu);
+                    if (!err) err = std::current_exception();
+                }
+            }
+        };
+        const int nth = std::max(1, std::min(n, (int)std::max(1u, std::thread::hardware_concurrency())));
+        std::vector<std::thread> pool;
+        for (int t = 1; t < nth; ++t) pool.emplace_back(worker);
+        worker();
+        for (auto &t : pool) t.join();
+        if (err) std::rethrow_exception(err);
+        for (const Candidate &c : res) take(c);
+    } else if (o.slice_restarts <= 0 || o.slice_restarts >= restarts) {
         // every restart grows, anneals, slices and refines in turn; an annealed
         // stem can need more sliced edges than the budget allows (annealing
         // between picks keeps the width, it does not force it down), and the
         // greedy pipeline is then tried on the same grown stem
         for (int r = 0; r < restarts; ++r) {
-            const int seed = (r == 0) ? 0 : pick(rng);
+            const int seed = (r == 0) ? start0 : pick(rng);
             const double noise = (r == 0) ? 0.0 : 0.9;
             const std::vector<int> grown = grow_stem(B, seed, rng, noise);
             if (!slice_refine(seed, shape(seed, grown, anneal), anneal) && anneal > 0)
@@ -629,7 +685,7 @@ Scheme plan_scheme(const Network &net, const tn_plan_opts &o) {
         std::vector<Start> starts;
         for (int r = 0; r < restarts; ++r) {
             Start st;
-            st.seed = (r == 0) ? 0 : pick(rng);
+            st.seed = (r == 0) ? start0 : pick(rng);
             const double noise = (r == 0) ? 0.0 : 0.9;
             st.grown = grow_stem(B, st.seed, rng, noise);
             st.order = shape(st.seed, st.grown, anneal);

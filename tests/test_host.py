@@ -157,6 +157,43 @@ def test_two_phase_restarts_give_valid_schemes():
     assert math.log2(tc) == pytest.approx(info["log2_tc"], abs=1e-9)
 
 
+def _check_scheme_value(c, oq, cb, net, plan, limit):
+    info = P.tn_plan_info(plan)
+    assert info["cw"] <= limit
+    order, sl = P.tn_plan_export(plan)
+    edges = _oracle_edges(net)
+    onet = oracle.build_network(c, oq, cb)
+    sliced = [edges[e] for e in sl]
+    tot = oracle.contract_sliced_sum(onet, sliced, [tuple(x) for x in order])
+    np.testing.assert_allclose(tot.reshape(-1), oracle.sv_amplitudes(c, oq, cb), atol=1e-13)
+    tc, ocw = oracle.tree_cost(onet.edges, onet.open_edges, [tuple(x) for x in order], sliced)
+    assert ocw == info["cw"]
+    assert math.log2(tc) == pytest.approx(info["log2_tc"], abs=1e-9)
+    return order, sl, info
+
+
+def test_start_cluster_and_stem_start_sweep():
+    # start_cluster picks the first restart's stem seed; stem_starts grows
+    # stems from spread start clusters on the host's threads. Every scheme
+    # must meet the width and equal the state vector; the sweep must not
+    # depend on scheduling (two runs agree).
+    c = random_circuit(grid_layout(3, 4), 8, 91)
+    oq = [0, 7]
+    net, cb = _net(c, oq, 23)
+    exports = set()
+    for start in (0, 5, 11):
+        plan = P.tn_plan_create(net, cw_limit=6, restarts=1, start_cluster=start, anneal_iters=5000)
+        order, sl, _ = _check_scheme_value(c, oq, cb, net, plan, 6)
+        exports.add((order.tobytes(), sl.tobytes()))
+    assert len(exports) > 1  # different start clusters, different stems
+    runs = []
+    for _ in range(2):
+        plan = P.tn_plan_create(net, cw_limit=6, stem_starts=12, anneal_iters=5000)
+        order, sl, info = _check_scheme_value(c, oq, cb, net, plan, 6)
+        runs.append((order.tobytes(), sl.tobytes(), info["log2_tc"]))
+    assert runs[0] == runs[1]
+
+
 def test_network_info_wire_segments():
     c = random_circuit(grid_layout(2, 2), 2, 9)
     net, _ = _net(c, [1], 3)
