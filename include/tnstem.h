@@ -111,6 +111,12 @@ typedef struct {
                                  there are fewer), each annealed, sliced and
                                  refined on the host's threads; the cheapest
                                  scheme wins, whatever the thread count (0 = off) */
+    double width_area_weight; /* > 0: the unsliced stem anneal also scores this
+                                 weight times the stem's excess width summed
+                                 over its tensors (sum of max(0, rank -
+                                 cw_limit)), so stems that stay wide only
+                                 briefly win; pays where slicing must remove
+                                 many bits of width (0 = off) */
 } tn_plan_opts;
 
 typedef struct {

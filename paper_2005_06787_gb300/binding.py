@@ -57,7 +57,8 @@ class tn_plan_opts(C.Structure):
                 ("gemm_min_kn", C.c_int32), ("merge_group", C.c_int32),
                 ("merge_rank_cap", C.c_int32), ("anneal_iters", C.c_int32),
                 ("slice_restarts", C.c_int32), ("seed", C.c_uint64),
-                ("start_cluster", C.c_int32), ("stem_starts", C.c_int32)]
+                ("start_cluster", C.c_int32), ("stem_starts", C.c_int32),
+                ("width_area_weight", C.c_double)]
 
 
 class tn_plan_stats(C.Structure):
@@ -240,10 +241,10 @@ def make_opts(**kw) -> tn_plan_opts:
     defaults = dict(cw_limit=30, min_sliced=0, max_sliced=40, restarts=8, local_opt_iters=4,
                     branch_rank=4, slice_batch=0, tile_bits=0, max_pass_steps=0, gemm_min_kn=0,
                     merge_group=0, merge_rank_cap=0, anneal_iters=0, slice_restarts=0, seed=0x5EED,
-                    start_cluster=0, stem_starts=0)
+                    start_cluster=0, stem_starts=0, width_area_weight=0.0)
     defaults.update(kw)
     for k, v in defaults.items():
-        setattr(o, k, int(v))
+        setattr(o, k, float(v) if k == "width_area_weight" else int(v))
     return o
 
 

@@ -287,11 +287,14 @@ static void local_opt_sweeps(const std::vector<Bits> &B, int seed, std::vector<i
 // to `window` places away; only the stem tensors between the two places
 // change, so a move is scored by recomputing that stretch. Score: log2 of
 // the stem cost plus one unit per bit the widest stem tensor exceeds the
-// limit (each such bit costs about one more sliced edge). Metropolis
+// limit (each such bit costs about one more sliced edge), plus area_w times
+// the excess width summed over all stem tensors (how long the stem stays
+// wide, which decides how many sliced edges it will need). Metropolis
 // acceptance at a temperature falling geometrically from t0 to t1.
 static void anneal_order(const std::vector<Bits> &B, int seed, std::vector<int> &order,
                          const Bits &sliced, int limit, long iters, std::mt19937_64 &rng,
-                         double t0 = 1.0, double t1 = 0.02, int window = 48, int cap_rank = 1 << 30) {
+                         double t0 = 1.0, double t1 = 0.02, int window = 48, int cap_rank = 1 << 30,
+                         double area_w = 0.0) {
     const int L = (int)order.size();
     if (L < 3 || iters <= 0) return;
     std::vector<Bits> Bs(B.size());
@@ -310,8 +313,14 @@ static void anneal_order(const std::vector<Bits> &B, int seed, std::vector<int> 
     double total = 0;
     for (double c : cost) total += c;
     auto max_rank = [&](const std::vector<int> &r) { return *std::max_element(r.begin(), r.end()); };
+    auto area = [&](const std::vector<int> &r) {
+        double a = 0;
+        if (area_w > 0)
+            for (int v : r) a += std::max(0, v - limit);
+        return area_w * a;
+    };
     auto score = [&](double tot, int mr) { return std::log2(tot) + std::max(0, mr - limit); };
-    double cur = score(total, max_rank(rank));
+    double cur = score(total, max_rank(rank)) + area(rank);
     std::vector<int> best_order = order;
     double best = cur;
     std::uniform_real_distribution<double> U(0.0, 1.0);
@@ -347,7 +356,7 @@ static void anneal_order(const std::vector<Bits> &B, int seed, std::vector<int> 
         for (size_t t = 1; t < seg.size(); ++t) nrank[(size_t)lo + t] = npre[t].count();
         const double ntotal = total - old_part + new_part;
         const int nmax = max_rank(nrank);
-        const double nscore = score(ntotal, nmax);
+        const double nscore = score(ntotal, nmax) + area(nrank);
         const double d = nscore - cur;
         if (nmax <= cap_rank && (d <= 0 || U(rng) < std::exp(-d / T))) {
             std::copy(seg.begin(), seg.end(), order.begin() + lo);
@@ -614,7 +623,7 @@ Scheme plan_scheme(const Network &net, const tn_plan_opts &o) {
     // unsliced anneal + window optimisation of a grown stem
     auto shape_with = [&](int seed, std::vector<int> order, long ann, std::mt19937_64 &r) {
         Bits none(net.n_edges());
-        anneal_order(B, seed, order, none, limit, ann, r);
+        anneal_order(B, seed, order, none, limit, ann, r, 1.0, 0.02, 48, 1 << 30, o.width_area_weight);
         local_opt_sweeps(B, seed, order, none, limit, lo_iters, 0);
         return order;
     };

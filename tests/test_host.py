@@ -194,6 +194,17 @@ def test_start_cluster_and_stem_start_sweep():
     assert runs[0] == runs[1]
 
 
+def test_width_area_weight_gives_valid_schemes():
+    # the unsliced anneal's excess-width term changes the stems it prefers;
+    # the schemes must still meet the width and equal the state vector
+    c = random_circuit(grid_layout(3, 4), 8, 91)
+    oq = [0, 7]
+    net, cb = _net(c, oq, 23)
+    for w in (0.05, 0.5):
+        plan = P.tn_plan_create(net, cw_limit=5, restarts=3, anneal_iters=5000, width_area_weight=w)
+        _check_scheme_value(c, oq, cb, net, plan, 5)
+
+
 def test_network_info_wire_segments():
     c = random_circuit(grid_layout(2, 2), 2, 9)
     net, _ = _net(c, [1], 3)
