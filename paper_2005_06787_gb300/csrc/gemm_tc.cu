@@ -7,7 +7,12 @@
 // column) gives C as interleaved complex [M][2N]. Precision options split
 // each FP32 operand into hi + lo parts of the tensor-core type and sum
 // hi*hi + hi*lo + lo*hi (x3), or use one rounded product (x1), always with
-// FP32 accumulation in tensor memory.
+// FP32 accumulation in tensor memory. In the x3 modes hi*hi accumulates in one
+// TMEM region and the two correction products in a second one; the epilogue
+// adds the two in FP32 with round-to-nearest. The tensor core's own FP32
+// accumulation truncates toward zero, so every product chained into the
+// accumulator that holds the full-size value costs a bias of about half an
+// ulp; keeping the corrections (2^-11 smaller) apart leaves one such chain.
 //
 // One block of 128 threads computes a 128-row tile of C for one batch item
 // and up to 256 real output columns: threads load A and B, split and write
@@ -95,6 +100,18 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
     return false;
 }
 
+// 32 lanes x 16 consecutive 32-bit TMEM columns into registers (warp-wide).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+        "%13,%14,%15}, [%16];\n"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+          "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+
 // Split an FP32 value into the tensor-core type: hi = x rounded to nearest,
 // lo = the remainder rounded to nearest (x3 modes). Rounding both parts
 // (rather than truncating) keeps the split unbiased, so errors of successive
@@ -169,7 +186,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_cgemm_kernel(TcArgs g) {
     const int tid = threadIdx.x, warp = tid >> 5;
 
     uint32_t ncols = 32;
-    while ((int)ncols < nbp) ncols <<= 1;
+    while ((int)ncols < (X3 ? 2 : 1) * nbp) ncols <<= 1;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
                          smem_u32(&tmem_base)),
@@ -248,11 +265,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_cgemm_kernel(TcArgs g) {
                 const uint64_t bhi = make_desc(smem_u32(sBhi) + kb);
                 const uint32_t first = (ch == 0 && ks == 0) ? 0u : 1u;
                 mma<KIND>(tmem, ahi, bhi, idesc, first);
-                if constexpr (X3) {
+                if constexpr (X3) {  // corrections in their own accumulator
                     const uint64_t alo = make_desc(smem_u32(sAlo) + kb);
                     const uint64_t blo = make_desc(smem_u32(sBlo) + kb);
-                    mma<KIND>(tmem, ahi, blo, idesc, 1u);
-                    mma<KIND>(tmem, alo, bhi, idesc, 1u);
+                    mma<KIND>(tmem + (uint32_t)nbp, ahi, blo, idesc, first);
+                    mma<KIND>(tmem + (uint32_t)nbp, alo, bhi, idesc, 1u);
                 }
             }
             asm volatile(
@@ -275,14 +292,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_cgemm_kernel(TcArgs g) {
         for (int c0 = 0; c0 < nbp; c0 += 16) {
             uint32_t v[16];
             const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
-                "%13,%14,%15}, [%16];\n"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
-                  "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
-                  "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-                : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+            tmem_ld16(taddr, v);
+            if constexpr (X3) {
+                uint32_t w[16];
+                tmem_ld16(taddr + (uint32_t)nbp, w);
+#pragma unroll
+                for (int q = 0; q < 16; ++q)
+                    v[q] = __float_as_uint(__fadd_rn(__uint_as_float(v[q]), __uint_as_float(w[q])));
+            }
             if (row < g.M) {
                 for (int q = 0; q < 16; ++q) {
                     const int col = n0 + c0 + q;
@@ -340,8 +357,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_cgemm_persistent(TcArgs g, i
     const int tid = threadIdx.x, warp = tid >> 5;
     const int64_t mtiles = (g.M + TC_BM - 1) / TC_BM;
     const int64_t n_tiles = mtiles * n_items;
+    constexpr int NACC = X3 ? 2 : 1;  // TMEM regions per accumulator (main, corrections)
     uint32_t ncols = 32;
-    while ((int)ncols < 2 * nbp) ncols <<= 1;
+    while ((int)ncols < 2 * NACC * nbp) ncols <<= 1;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
                          smem_u32(&tmem_base)), "r"(ncols));
@@ -432,7 +450,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_cgemm_persistent(TcArgs g, i
     };
     auto issue = [&](int st, int acc) {
         asm volatile("tcgen05.fence::after_thread_sync;\n");
-        const uint32_t d = tmem + (uint32_t)(acc * nbp);
+        const uint32_t d = tmem + (uint32_t)(acc * NACC * nbp);
         const int nks = (K2 + KSTEP - 1) / KSTEP;  // K steps covering 2K (padding is zero)
         for (int ks = 0; ks < nks; ++ks) {
             const uint32_t kb = (uint32_t)((ks * KSTEP) / KC);
@@ -440,11 +458,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_cgemm_persistent(TcArgs g, i
             const uint64_t ahi = make_desc(smem_u32(sA[st][0]) + kb * TC_BM * 128 + ko);
             const uint64_t bhi = make_desc(smem_u32(sB[0]) + kb * nbp * 128 + ko);
             mma<KIND>(d, ahi, bhi, idesc, ks == 0 ? 0u : 1u);
-            if constexpr (X3) {
+            if constexpr (X3) {  // corrections in their own accumulator
                 const uint64_t alo = make_desc(smem_u32(sA[st][1]) + kb * TC_BM * 128 + ko);
                 const uint64_t blo = make_desc(smem_u32(sB[1]) + kb * nbp * 128 + ko);
-                mma<KIND>(d, ahi, blo, idesc, 1u);
-                mma<KIND>(d, alo, bhi, idesc, 1u);
+                mma<KIND>(d + (uint32_t)nbp, ahi, blo, idesc, ks == 0 ? 0u : 1u);
+                mma<KIND>(d + (uint32_t)nbp, alo, bhi, idesc, 1u);
             }
         }
         asm volatile(
@@ -457,15 +475,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_cgemm_persistent(TcArgs g, i
         const int64_t row = m0 + warp * 32 + (tid & 31);
         for (int c0 = 0; c0 < nbp; c0 += 16) {
             uint32_t v[16];
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(acc * nbp + c0);
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
-                "%13,%14,%15}, [%16];\n"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
-                  "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
-                  "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-                : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+            const uint32_t taddr =
+                tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(acc * NACC * nbp + c0);
+            tmem_ld16(taddr, v);
+            if constexpr (X3) {
+                uint32_t w[16];
+                tmem_ld16(taddr + (uint32_t)nbp, w);
+#pragma unroll
+                for (int q = 0; q < 16; ++q)
+                    v[q] = __float_as_uint(__fadd_rn(__uint_as_float(v[q]), __uint_as_float(w[q])));
+            }
             if (row < g.M) {
                 if (c0 + 16 <= N2 && (N2 & 3) == 0) {
 #pragma unroll
@@ -560,7 +579,10 @@ cudaError_t run_tc(const TcArgs &a0, int64_t batch, tn_precision prec, cudaStrea
     if (!g_tc_err) return cudaErrorInitializationError;  // tc_gemm_init() not called
     a.err = g_tc_err;
     const int K2 = 2 * a.K, N2 = 2 * a.N;
-    if (K2 <= P_K2MAX && K2 % 4 == 0 && N2 <= TC_MAX_N2 && batch <= 65535 &&
+    // the persistent kernel holds two accumulators of (x3: two regions of) nbp
+    // TMEM columns each within the SM's 512
+    const int n2_max_persistent = prec == TN_PREC_BF16x1 ? TC_MAX_N2 : TC_MAX_N2 / 2;
+    if (K2 <= P_K2MAX && K2 % 4 == 0 && N2 <= n2_max_persistent && batch <= 65535 &&
         tc_persistent_smem((int)prec, K2, N2) <= P_SMEM_MAX) {
         static int num_sms = 0;
         if (!num_sms) {
@@ -574,7 +596,7 @@ cudaError_t run_tc(const TcArgs &a0, int64_t batch, tn_precision prec, cudaStrea
         // each holds 2 x 2N <= 512 TMEM columns in total)
         int per_sm = (int)std::max<size_t>(1, std::min<size_t>(4, (228 * 1024) / (smem + 1024)));
         int ncols = 32;
-        while (ncols < 2 * ((N2 + 15) & ~15)) ncols <<= 1;
+        while (ncols < (prec == TN_PREC_BF16x1 ? 2 : 4) * ((N2 + 15) & ~15)) ncols <<= 1;
         per_sm = std::max(1, std::min(per_sm, 512 / ncols));  // TMEM: 512 columns per SM
         const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)num_sms * per_sm));
         switch (prec) {
