@@ -10,9 +10,13 @@ slice.
 
 Also measured in the same run: the plain FP32 path (per step a permute then a
 SIMT GEMM, one slice per launch), per-launch CUDA-event timings of one batch
-(roofline of the dominant kernel), the same call with host buffers (e2e), SM
-clocks during the timed region, and the FP64 CPU oracle on a bounded sample
-of the same workload.
+(roofline of the dominant kernel, against the measured HBM copy rate and the
+FP32 FMA rate the library's own microkernel reaches), the same call with host
+buffers (e2e), SM clocks during the timed region, parity of slices 0 and 1
+against FP64 oracle values stored under tests/golden (written by scripts that
+call only the oracle), the error of each GEMM precision beside its speed, the
+plain cost model's plan pick timed beside the learned model's, and the FP64
+CPU oracle on a bounded sample of the same workload (its heaviest stem steps).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
                     [--impl reference]
@@ -143,31 +147,71 @@ class ClockSampler:
 
 # ------------------------------------------------------------- CPU oracle
 
-def oracle_sample(name: str, budget_s: float, order=None, sliced_wires=None, plan_info=None):
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+def stored_scheme(name: str):
+    """Order and sliced wire segments of the workload's plan, as exported by
+    tests/golden/make_scheme.py (schedule input for the oracle), or None."""
+    path = os.path.join(GOLDEN, f"{name}_scheme.json")
+    if not os.path.exists(path):
+        return None
+    sch = json.load(open(path))
+    return [tuple(p) for p in sch["order"]], [tuple(w) for w in sch["sliced_wires"]]
+
+
+def stored_slices(name: str):
+    """FP64 oracle values of stored slices {slice id: complex array} and the
+    seconds each took when the script wrote them, or (None, None)."""
+    path = os.path.join(GOLDEN, f"{name}_slices.json")
+    if not os.path.exists(path):
+        return None, None
+    g = json.load(open(path))
+    vals = {int(k): np.asarray(v["re"]) + 1j * np.asarray(v["im"]) for k, v in g["slices"].items()}
+    secs = {int(k): v.get("seconds") for k, v in g["slices"].items()}
+    return vals, {"seconds": secs, "threads": g.get("threads")}
+
+
+def oracle_sample(name: str, budget_s: float, order, sliced_wires, max_rank: int = 27):
     """Time the FP64 oracle on a bounded sample of the workload: the pairwise
-    contractions of slice 0 along the plan's order, in order, until the time
-    budget is spent. Returns (stem-tc done, seconds, steps done)."""
+    contraction steps of slice 0 with the largest contraction cost 2^|E_AB|
+    (where a slice's time goes) among those whose tensors have at most
+    max_rank edges, heaviest first, each on inputs of its true shape filled
+    with a constant (the oracle's loops do not depend on the values), until
+    the time budget is spent. Returns (tc done, seconds, steps done, tc of the
+    whole slice)."""
     import oracle
     c, oq, cb = workload_inputs(name)
     net = oracle.build_network(c, oq, cb)
     if sliced_wires:
         net = oracle.fix_edges(net, oracle.slice_assignment(sliced_wires, 0))
-    live = {i: (T, list(el)) for i, (T, el) in enumerate(zip(net.tensors, net.edges))}
+    # replay the order on edge lists (no arithmetic) for each step's shapes
+    live = {i: list(el) for i, el in enumerate(net.edges)}
     N = len(net.tensors)
-    tc = 0.0
-    done = 0
-    t0 = time.perf_counter()
+    steps = []
+    slice_tc = 0.0
     for k, (a, b) in enumerate(order):
-        A, ea = live.pop(int(a))
-        B, eb = live.pop(int(b))
-        eab = len(set(ea) | set(eb))
-        Cm, ec = oracle.contract_pair(A, ea, B, eb)
-        live[N + k] = (Cm, ec)
-        tc += 2.0 ** eab
+        ea, eb = live.pop(int(a)), live.pop(int(b))
+        sb, sa = set(eb), set(ea)
+        ec = [e for e in ea if e not in sb] + [e for e in eb if e not in sa]
+        if max(len(ea), len(eb), len(ec)) <= max_rank:
+            steps.append((len(sa | sb), ea, eb))
+        slice_tc += 2.0 ** len(sa | sb)
+        live[N + k] = ec
+    tc = secs = 0.0
+    done = 0
+    for n, ea, eb in sorted(steps, key=lambda x: -x[0]):
+        A = np.full((2,) * len(ea), 0.5 + 0.25j)
+        B = np.full((2,) * len(eb), 0.5 - 0.25j)
+        t0 = time.perf_counter()
+        oracle.contract_pair(A, ea, B, eb)
+        secs += time.perf_counter() - t0
+        tc += 2.0 ** n
         done += 1
-        if time.perf_counter() - t0 > budget_s:
+        del A, B
+        if secs > budget_s:
             break
-    return tc, time.perf_counter() - t0, done
+    return tc, secs, done, slice_tc
 
 
 def oracle_threads() -> int:
@@ -192,17 +236,16 @@ def dist_env():
     return rank, world, local
 
 
-# FP32 FMA peak of one GB300, from unit counts and clock: 152 SMs x 128 FP32
-# lanes x 2 flops x 2.07 GHz (maximum SM clock). A microbenchmark of
-# independent FFMA chains reached 74.4 TFLOP/s (92 %) on the GB300s.
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# FP32 FMA rate from unit counts and clock (152 SMs x 128 FP32 lanes x 2 flops
+# x 2.07 GHz): used only when the library's measured rate is unavailable.
+FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
-# DRAM traffic of the dominant kernel, from one ncu capture of this bench's
-# launches (profiles/launches_diag53_m14.md: dram__bytes_read.sum +
-# dram__bytes_write.sum over the pass launches of one batch). It describes
-# the kernel source and plan it was taken on: with any other kernels.cu or
-# plan the bench reports traffic as null.
+# DRAM traffic of the dominant kernel from one earlier ncu capture of this
+# bench's pass launches (dram__bytes_read.sum + dram__bytes_write.sum over one
+# batch), keyed on the sha of kernels.cu and on the plan it was taken on: a
+# stored number, not measured in this run, and null for any other kernel
+# source or plan.
 TRAFFIC_CAPTURE = {"kernels_sha256": "8e2fd62c548759d5", "workload": "diag53_m14", "pass_launches": 44,
                    "log2_tc_total": 45.640, "dram_bytes_per_batch": 145.43e9}
 
@@ -266,50 +309,48 @@ def sampling_run(stream, job_seconds: float, n_open: int, M: float = 10.0):
 
 
 def run_reference(args):
-    """The oracle arm: FP64 CPU contraction of bounded samples of the same
-    workload (each step one bounded sample), same metric and units."""
+    """The oracle arm: the FP64 CPU oracle on bounded samples of the same
+    workload (each step one bounded sample: the heaviest stem steps of slice
+    0, see oracle_sample), same metric and units. It reads the stored scheme
+    and never loads the GPU library."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
     import oracle
     oracle.build()
     name = args.workload
-    cfg_plan = _host_plan(name)
-    order, wires, info = cfg_plan
+    sch = stored_scheme(name)
+    if sch is None:
+        print(json.dumps({"impl": "reference", "unavailable": f"no stored scheme for {name}"}), flush=True)
+        return
+    order, wires = sch
     steps = []
-    budget = max(2.0, args.ref_budget / max(1, args.steps + args.warmup))
+    budget = max(1.0, args.ref_budget / max(1, args.steps + args.warmup))
+    slice_tc = None
     for i in range(args.warmup + args.steps):
-        tc, secs, done = oracle_sample(name, budget, order, wires, info)
+        tc, secs, done, slice_tc = oracle_sample(name, budget, order, wires)
         if i >= args.warmup:
             steps.append((tc, secs, done))
-    tc = sum(s[0] for s in steps)
-    secs = sum(s[1] for s in steps)
+    tc = sum(st[0] for st in steps)
+    secs = sum(st[1] for st in steps)
     tflops = 8.0 * tc / secs / 1e12
-    slices = tc / info["stem_tc_per_slice"] / secs
+    slices = tc / slice_tc / secs
+    _, rec = stored_slices(name)
     line = {"impl": "reference", "metric": METRIC, "value": tflops, "unit": "TFLOP/s",
             "slices_per_s": slices, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * secs / max(1, len(steps)), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": name, "n_qubits": 53, "cycles": CONFIGS[name]["cycles"],
-                       "n_open": CONFIGS[name]["n_open"], "cw": info["cw"]},
+                       "n_open": CONFIGS[name]["n_open"]},
             "cpu_baseline": {"value": tflops, "unit": "TFLOP/s", "cores": oracle_threads(),
                              "kind": "oracle",
-                             "sample": f"pairwise FP64 contractions of slice 0 along the plan's "
-                                       f"order, {budget:.0f} s per step"},
+                             "sample": f"FP64 pairwise contractions of slice 0: its heaviest steps "
+                                       f"with tensors of at most 2^27 entries, {budget:.1f} s per "
+                                       f"step (slices/s = tc rate / the slice's tc {slice_tc:.3e})",
+                             "whole_slice_seconds_when_stored": rec},
             "e2e": {"value": tflops, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
-
-
-def _host_plan(name):
-    import paper_2005_06787_gb300 as P
-    c, oq, cb = workload_inputs(name)
-    net = P.tn_build_network(c, oq, cb)
-    plan = P.tn_plan_create(net, **plan_options(name))
-    order, sl = P.tn_plan_export(plan)
-    _, _, q, s = net.info()
-    wires = [(int(q[e]), int(s[e])) for e in sl]
-    return order, wires, P.tn_plan_info(plan)
 
 
 def run_configs(args):
@@ -503,11 +544,11 @@ def main():
     if args.warmup < 3:
         args.warmup = 3
     sys.path.insert(0, ROOT)
-    from paper_2005_06787_gb300._build import build as build_lib
-    build_lib()
     if args.impl == "reference":
         run_reference(args)
         return
+    from paper_2005_06787_gb300._build import build as build_lib
+    build_lib()
     if args.learned:
         run_learned(args)
         return
@@ -560,6 +601,11 @@ def main():
     plan_s = time.perf_counter() - t0
     P.tn_plan_prepare(plan, stream=stream)
     torch.cuda.synchronize()
+    try:
+        fp32_peak, n_sms = P.tn_fp32_fma_peak(stream)
+        fp32_src = f"measured: FMA-chain microkernel of the library on {n_sms} SMs"
+    except P.TnError:
+        fp32_peak, fp32_src = FP32_NOMINAL_TFLOPS, "nominal (152 SMs x 128 lanes x 2 x 2.07 GHz)"
     info = P.tn_plan_info(plan)
     SB = info["batch_items"] // max(info["n_prefixes"], 1)
     n_slices_total = 1 << info["n_sliced"]
@@ -655,57 +701,144 @@ def main():
     tflops_simt = d["flops"] / (d["ms"] / 1e3) / 1e12
     tot_ms = sum(v["ms"] for v in by_kind.values())
     # Each pass launch is bounded by HBM (its bytes at the measured copy rate)
-    # or by FP32 FMA arithmetic (its flops at FP32_PEAK_TFLOPS); the bound of
-    # the kernel is the side that holds more of the launches' ideal time.
+    # or by FP32 FMA arithmetic (its flops at the FMA rate the library's
+    # microkernel measured on this GPU); the bound of the kernel is the side
+    # that holds more of the launches' ideal time.
     t_hbm = t_alu = t_ideal = 0.0
     for r in recs:
         if r["kind"] != 0:
             continue
         a = r["bytes"] / (peaks["hbm_gbs"] * 1e9)
-        b = r["flops"] / (FP32_PEAK_TFLOPS * 1e12)
+        b = r["flops"] / (fp32_peak * 1e12)
         t_ideal += max(a, b)
         if a >= b:
             t_hbm += a
         else:
             t_alu += b
     if t_alu > t_hbm:
-        roofline = {"bound": "alu", "achieved": tflops_simt, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": tflops_simt / FP32_PEAK_TFLOPS, "peak_source": "derived (FP32 FMA units x clock)"}
+        roofline = {"bound": "alu", "achieved": tflops_simt, "peak": fp32_peak, "unit": "TFLOP/s",
+                    "frac": tflops_simt / fp32_peak, "peak_source": fp32_src}
     else:
         roofline = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": gbs / peaks["hbm_gbs"], "peak_source": peak_kind}
-    roofline.update({"traffic": pass_traffic(name, info),
+    traffic = pass_traffic(name, info)
+    traffic_src = (f"stored ncu capture (kernels.cu sha {TRAFFIC_CAPTURE['kernels_sha256']}, "
+                   f"{TRAFFIC_CAPTURE['pass_launches']} pass launches of this plan)") if traffic else None
+    roofline.update({"traffic": traffic,
                      "algorithmic_bytes_per_launch": d["bytes"] / d["launches"], "kernel": "pass_kernel",
                      "share_of_step": d["ms"] / tot_ms if tot_ms else None,
                      "hbm_gbs": gbs, "hbm_frac": gbs / peaks["hbm_gbs"], "simt_tflops": tflops_simt,
-                     "fp32_frac": tflops_simt / FP32_PEAK_TFLOPS,
+                     "fp32_frac": tflops_simt / fp32_peak, "fp32_peak_tflops": fp32_peak,
+                     "fp32_peak_source": fp32_src, "traffic_source": traffic_src,
                      "roofline_time_frac": t_ideal / (d["ms"] / 1e3) if d["ms"] else None})
 
     order_export, sl_export = P.tn_plan_export(plan)
+    _, _, q_of, s_of = net.info()
+    eid = {(int(a), int(b)): e for e, (a, b) in enumerate(zip(q_of, s_of))}
+    bench_wires = [(int(q_of[e]), int(s_of[e])) for e in sl_export]
+    sch = stored_scheme(name)
+    gold, gold_rec = stored_slices(name)
+
+    def stored_plan(**kw):
+        order, wires = sch
+        return P.tn_plan_create(net, order=order, sliced_edges=[eid[w] for w in wires], **dict(popts, **kw))
+
+    def rel_l2(a, b):
+        return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+    def slice_amps(pl, sid, prec="fp32", buf=None):
+        buf = torch.zeros(2 * nb, dtype=torch.float64, device="cuda") if buf is None else buf
+        P.tn_contract_stem(pl, sid, sid + 1, buf, prec=prec, stream=stream)
+        torch.cuda.synchronize()
+        return buf.cpu().numpy().view(np.complex128)
+
+    # parity of the timed configuration: slices 0 and 1 against the stored
+    # FP64 oracle values (Supp. A.1 "Slicing": a slice is the sub-network with
+    # its sliced wires fixed); the timed plan itself when its scheme is the
+    # stored one, else the stored scheme with the timed plan's launch options
+    parity = None
+    if rank == 0 and sch is not None and gold:
+        same = ([tuple(map(int, x)) for x in order_export] == [tuple(x) for x in sch[0]]
+                and bench_wires == list(sch[1]))
+        pick = (choice or {}).get("pick") or {}
+        pplan = plan if same else stored_plan(**{k: pick[k] for k in ("tile_bits", "max_pass_steps",
+                                                                      "merge_group") if k in pick})
+        if not same:
+            P.tn_plan_prepare(pplan, stream=stream)
+        errs = {str(sid): rel_l2(slice_amps(pplan, sid), ref) for sid, ref in sorted(gold.items())}
+        parity = {"rel_l2_fp32": max(errs.values()), "per_slice": errs, "tolerance": 1e-5,
+                  "same_scheme_as_timed_plan": same,
+                  "reference": "FP64 oracle slices stored by tests/golden/make_stored_slices.py",
+                  "oracle_whole_slice_seconds_when_stored": gold_rec}
+        del pplan
+
+    # the plain cost model's pick timed beside the chosen one (Sec. 4 scores
+    # schemes by a cost function; here two cost models pick among candidates)
+    if rank == 0 and choice is not None:
+        keys = ("seed", "tile_bits", "max_pass_steps", "merge_group")
+        fp_pick = choice["plain_model_pick"]
+        if all(choice["pick"][k] == fp_pick[k] for k in keys):
+            choice["measured_gain"] = 1.0
+            choice["measured_gain_note"] = "both cost models picked the same candidate"
+        else:
+            t_pick = time.perf_counter()
+            if fp_pick["seed"] == choice["pick"]["seed"]:  # same scheme, other launch options
+                fplan = P.tn_plan_create(net, order=[tuple(map(int, x)) for x in order_export],
+                                         sliced_edges=list(sl_export),
+                                         **dict(popts, **{k: fp_pick[k] for k in keys[1:]}))
+            else:
+                fplan = P.tn_plan_create(net, **dict(popts, **{k: fp_pick[k] for k in keys}))
+            P.tn_plan_prepare(fplan, stream=stream)
+            fsb = P.tn_plan_info(fplan)["batch_items"]
+            fout = torch.zeros(2 * nb, dtype=torch.float64, device="cuda")
+            P.tn_contract_stem(fplan, 0, fsb, fout, stream=stream)
+            torch.cuda.synchronize()
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            nfs = max(2, min(args.steps, 6))
+            f0.record(stream)
+            for i in range(nfs):
+                P.tn_contract_stem(fplan, (1 + i) * fsb, (2 + i) * fsb, fout, stream=stream)
+            f1.record(stream)
+            torch.cuda.synchronize()
+            f_sps = nfs * fsb / (f0.elapsed_time(f1) / 1e3)
+            choice["plain_model_pick_slices_per_s"] = f_sps
+            choice["measured_gain"] = slices_per_s / f_sps
+            choice["plain_model_pick_seconds"] = time.perf_counter() - t_pick
+            del fplan
+        torch.cuda.empty_cache()
+
     # precision sweep on a branch-merged plan (Supp. A.3): most steps become
-    # GEMM steps, run by the FP32 SIMT GEMM or the tcgen05 GEMM per precision
+    # GEMM steps, run by the FP32 SIMT GEMM or the tcgen05 GEMM per precision;
+    # each precision's speed beside its error against the stored FP64 slices
     sweep = None
     if rank == 0 and not args.no_sweep:
         del plan
         torch.cuda.empty_cache()
-        mplan = P.tn_plan_create(net, **dict(popts, merge_group=3))
+        mplan = stored_plan(merge_group=3) if (sch is not None and gold) else \
+            P.tn_plan_create(net, **dict(popts, merge_group=3))
         P.tn_plan_prepare(mplan, stream=stream)
         minfo = P.tn_plan_info(mplan)
         mflops = 8.0 * minfo["stem_tc_per_slice"]
         peaks_all, _ = measured_peaks()
         sweep = {"plan": {"merge_group": 3, "stem_steps": minfo["n_stem_steps"],
-                          "gemm_steps": minfo["n_gemm_steps"], "stem_tc_per_slice": minfo["stem_tc_per_slice"]}}
+                          "gemm_steps": minfo["n_gemm_steps"], "stem_tc_per_slice": minfo["stem_tc_per_slice"],
+                          "scheme": "stored" if (sch is not None and gold) else "planned"}}
+        bufs = [torch.zeros(2 * nb, dtype=torch.float64, device="cuda") for _ in range(3)]
         for prec in ("fp32", "tf32x3", "bf16x3", "bf16x1"):
-            P.tn_contract_stem(mplan, 0, 1, out, prec=prec, stream=stream)
+            P.tn_contract_stem(mplan, 0, 1, bufs[0], prec=prec, stream=stream)
             torch.cuda.synchronize()
             q0 = torch.cuda.Event(enable_timing=True)
             q1 = torch.cuda.Event(enable_timing=True)
             q0.record(stream)
             for i in range(2):
-                P.tn_contract_stem(mplan, 1 + i, 2 + i, out, prec=prec, stream=stream)
+                P.tn_contract_stem(mplan, 1 + i, 2 + i, bufs[1 + i], prec=prec, stream=stream)
             q1.record(stream)
             torch.cuda.synchronize()
             sps = 2 / (q0.elapsed_time(q1) / 1e3)
+            err = None
+            if gold and sweep["plan"]["scheme"] == "stored":
+                got = {0: bufs[0].cpu().numpy().view(np.complex128), 1: bufs[1].cpu().numpy().view(np.complex128)}
+                err = max(rel_l2(got[sid], gold[sid]) for sid in (0, 1) if sid in gold)
             recs = P.tn_plan_profile(mplan, 0, prec=prec, mode="fused", stream=stream)
             g = [r for r in recs if r["kind"] == 1]
             gms = sum(r["ms"] for r in g)
@@ -714,23 +847,25 @@ def main():
             mult = {"fp32": 1, "tf32x3": 3, "bf16x3": 3, "bf16x1": 1}[prec]
             peak = peaks_all.get("bf16_tflops", 1900.0) * (0.5 if prec == "tf32x3" else 1.0)
             sweep[prec] = {"slices_per_s": sps, "stem_tflops": sps * mflops / 1e12,
+                           "rel_l2_vs_fp64_oracle": err,
                            "gemm_share": gms / sum(r["ms"] for r in recs),
                            "gemm_alg_tflops": gtf,
                            "gemm_exec_frac_of_tensor_peak": (gtf * mult / peak) if (gtf and prec != "fp32") else None}
-        del mplan
+            if parity is not None and err is not None:
+                parity[f"rel_l2_{prec}_merged_plan"] = err
+        del mplan, bufs
         torch.cuda.empty_cache()
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        order, sl = order_export, sl_export
-        _, _, q, s = net.info()
-        wires = [(int(q[e]), int(s[e])) for e in sl]
-        tc, secs, done = oracle_sample(name, args.cpu_budget, order, wires, info)
+        order, wires = sch if sch is not None else ([tuple(map(int, x)) for x in order_export], bench_wires)
+        tc, secs, done, slice_tc = oracle_sample(name, args.cpu_budget, order, wires)
         cpu_tflops = 8.0 * tc / secs / 1e12
         cpu = {"value": cpu_tflops, "unit": "TFLOP/s", "cores": oracle_threads(), "kind": "oracle",
-               "slices_per_s": tc / info["stem_tc_per_slice"] / secs,
-               "sample": f"FP64 pairwise contractions of slice 0 along the plan's order: "
-                         f"first {done} of {len(order)} pairs in {secs:.1f} s"}
+               "slices_per_s": tc / slice_tc / secs,
+               "sample": f"FP64 pairwise contractions of slice 0: its {done} heaviest steps with "
+                         f"tensors of at most 2^27 entries ({tc:.3e} of the slice's {slice_tc:.3e} "
+                         f"tc) in {secs:.1f} s"}
 
     # passes, GEMM steps, accumulate, advance, finalize, and one staging
     # kernel before each pass that reads its branch matrices from the constant bank
@@ -768,6 +903,7 @@ def main():
             "launch_breakdown": by_kind,
             "plain_breakdown": plain_kind,
             "cpu_baseline": cpu,
+            "parity": parity,
             "precision_sweep": sweep,
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks,

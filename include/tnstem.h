@@ -184,8 +184,11 @@ tn_status tn_plan_create(tn_network *net, const int32_t *order, int32_t n_pairs,
 
 /* Upload leaves for n_prefixes bitstring prefixes (n_prefixes * n_closed
  * bytes; NULL = the network's own prefix) and pre-compute every branch on
- * the device, once (Supp. A.3, "Pre-computation"). Allocates device memory.
- * Must precede tn_contract_stem; may be called again to change prefixes. */
+ * the device, once (Supp. A.3, "Pre-computation"). Allocates device memory
+ * on the current CUDA device; tn_contract_stem, tn_contract_stem_noalloc and
+ * tn_plan_profile must then be called with that device current (else
+ * TN_ERR_INVALID_ARG). Must precede tn_contract_stem; may be called again to
+ * change prefixes. */
 tn_status tn_plan_prepare(tn_plan *plan, const uint8_t *prefixes, int32_t n_prefixes,
                           void *cuda_stream);
 
@@ -337,6 +340,14 @@ tn_status tn_frugal_sample(const double *amps_dev, const double *u_dev, const do
                            int64_t n_batches, int32_t batch_size, int32_t n_qubits, double M,
                            void *cuda_stream, int32_t *index_dev, int32_t *accepted_dev,
                            double *picked_dev);
+
+/* Roofline denominator of the fused stem pass (no counterpart in the paper,
+ * whose Table 1 efficiencies divide by a nominal 15.7 TFLOP/s): the FP32 FMA
+ * rate this GPU reaches, measured by a kernel of independent FMA chains on
+ * every SM (best of three timed launches after one warm-up, CUDA events on
+ * cuda_stream). Writes TFLOP/s (2 flops per FMA) to *tflops and the SM count
+ * to *sm_count (host pointers). Synchronises cuda_stream. */
+tn_status tn_fp32_fma_peak(void *cuda_stream, double *tflops, int32_t *sm_count);
 
 /* Sec. 2: linear XEB 2^n <p> - 1 of count amplitudes (interleaved re, im,
  * device memory), p = |amp|^2, computed in FP64 on the device. out is a host

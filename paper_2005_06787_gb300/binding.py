@@ -32,7 +32,7 @@ EXPORTED = [
     "tn_version", "tn_plan_features", "tn_mlp_create", "tn_mlp_n_params", "tn_mlp_set_params",
     "tn_mlp_get_params", "tn_mlp_loss_grad", "tn_mlp_train", "tn_mlp_predict", "tn_mlp_destroy",
     "tn_plan_search", "tn_set_prefix", "tn_destroy_plan", "tn_destroy_network", "tn_frugal_sample",
-    "tn_device_status",
+    "tn_device_status", "tn_fp32_fma_peak",
 ]
 N_FEATURES = 16
 
@@ -130,6 +130,7 @@ def load():
     L.tn_linear_xeb.argtypes = [vp, i64, i32, vp, C.POINTER(C.c_double)]
     L.tn_frugal_sample.argtypes = [vp, vp, vp, i64, i32, i32, C.c_double, vp, vp, vp, vp]
     L.tn_device_status.argtypes = []
+    L.tn_fp32_fma_peak.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(i32)]
     L.tn_permute.argtypes = [vp, vp, i32, vp, vp]
     L.tn_cgemm.argtypes = [vp, vp, vp, i64, i64, i64, i64, i64, i64, i64, C.c_int, vp]
     L.tn_plan_features.argtypes = [vp, C.c_int, C.c_int, vp, vp, i32, vp]
@@ -385,6 +386,15 @@ def tn_frugal_sample(amps_dev, u_dev, key_dev, n_batches: int, batch_size: int, 
 def tn_device_status() -> None:
     """Raise TnError(TN_ERR_TIMEOUT) if a bounded device-side wait gave up."""
     _check(load().tn_device_status())
+
+
+def tn_fp32_fma_peak(stream=None) -> Tuple[float, int]:
+    """Measured FP32 FMA rate of the current GPU (TFLOP/s) and its SM count."""
+    L = load()
+    tf = C.c_double()
+    sms = C.c_int32()
+    _check(L.tn_fp32_fma_peak(_stream(stream), C.byref(tf), C.byref(sms)))
+    return float(tf.value), int(sms.value)
 
 
 def tn_permute(inp, out, rank: int, perm: Sequence[int], stream=None):

@@ -374,6 +374,15 @@ tn_status tn_device_status(void) {
     });
 }
 
+tn_status tn_fp32_fma_peak(void *cuda_stream, double *tflops, int32_t *sm_count) {
+    return guard([&] {
+        if (!tflops || !sm_count) tn::fail(TN_ERR_INVALID_ARG, "null output");
+        int sms = 0;
+        TN_CUDA(tn::measure_fma_peak((cudaStream_t)cuda_stream, tflops, &sms));
+        *sm_count = sms;
+    });
+}
+
 tn_status tn_frugal_sample(const double *amps_dev, const double *u_dev, const double *key_dev,
                            int64_t n_batches, int32_t batch_size, int32_t n_qubits, double M,
                            void *cuda_stream, int32_t *index_dev, int32_t *accepted_dev,

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstring>
 #include <memory>
+#include <string>
 
 #include "plan.h"
 
@@ -97,6 +98,7 @@ void plan_prepare(Plan &p, const uint8_t *prefixes, int n_prefixes, cudaStream_t
         }
     p.release();
     TN_CUDA(init_kernels());
+    TN_CUDA(cudaGetDevice(&p.device));
     p.n_prefix = n_prefixes;
 
     // ---- leaf values per prefix (complex64), offsets per leaf
@@ -343,6 +345,15 @@ static void enqueue_plain_item(Plan &p, int pp, cudaStream_t st) {
                               p.d_comp, ba, 1, st));
 }
 
+void require_plan_device(const Plan &p) {
+    if (!p.prepared) fail(TN_ERR_INVALID_ARG, "plan not prepared (call tn_plan_prepare)");
+    int dev = -1;
+    TN_CUDA(cudaGetDevice(&dev));
+    if (dev != p.device)
+        fail(TN_ERR_INVALID_ARG, "the current CUDA device is " + std::to_string(dev) +
+                                     ", but the plan was prepared on device " + std::to_string(p.device));
+}
+
 static bool is_device_pointer(const void *ptr) {
     cudaPointerAttributes a{};
     if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
@@ -354,7 +365,7 @@ static bool is_device_pointer(const void *ptr) {
 
 void plan_contract(Plan &p, uint64_t s0, uint64_t s1, tn_precision prec, tn_exec_mode mode,
                    cudaStream_t st, double *amps_out, int accumulate) {
-    if (!p.prepared) fail(TN_ERR_INVALID_ARG, "plan not prepared (call tn_plan_prepare)");
+    require_plan_device(p);
     const int nsl = (int)p.scheme.sliced_list.size();
     const uint64_t total = nsl >= 63 ? ~0ull : (1ull << nsl);
     if (s0 > s1 || s1 > total) fail(TN_ERR_INVALID_ARG, "slice range outside [0, 2^n_sliced]");
@@ -420,7 +431,7 @@ static double step_flops(const Plan &p, int step) {
 
 std::vector<tn_launch_record> plan_profile(Plan &p, uint64_t s0, tn_precision prec,
                                           tn_exec_mode mode, cudaStream_t st) {
-    if (!p.prepared) fail(TN_ERR_INVALID_ARG, "plan not prepared (call tn_plan_prepare)");
+    require_plan_device(p);
     const int nsl = (int)p.scheme.sliced_list.size();
     const uint64_t total = nsl >= 63 ? ~0ull : (1ull << nsl);
     if (s0 >= total) fail(TN_ERR_INVALID_ARG, "slice_begin out of range");

@@ -732,10 +732,95 @@ cgemm_simt_kernel(GemmItemSrc g, int64_t M, int K, int N, int BM, int BN) {
     }
 }
 
+// Small K, N (branch absorption: K, N <= 8): a streaming kernel. Each thread
+// owns one row m: it reads A[m][0..K) (16-byte loads when rows and bases are
+// 16-byte aligned), multiplies by the K x N matrix held in shared memory and
+// writes C[m][0..N). The FMAs run in the order of cgemm_simt_kernel (kappa
+// ascending per output), so both kernels give identical results.
+template <int K, int N>
+__global__ void __launch_bounds__(G_THREADS) cgemm_rows_kernel(GemmItemSrc g, int64_t M, int vec_a,
+                                                               int vec_c) {
+    __shared__ float2 Bs[K * N];
+    const int64_t item = blockIdx.y;
+    const float2 *B;
+    if (g.use_batch) {
+        const int pl = (int)(item / g.ba.SB);
+        const int64_t s = g.ba.state->slice_base + (item - (int64_t)pl * g.ba.SB);
+        if (s >= g.ba.state->slice_end) return;  // uniform over the block
+        B = g.br ? g.pool + branch_offset(*g.br, g.ba.p0 + pl, s) : g.B + item * g.sB;
+    } else {
+        B = g.B + item * g.sB;
+    }
+    for (int i = threadIdx.x; i < K * N; i += G_THREADS) Bs[i] = B[i];
+    __syncthreads();
+    const float2 *A = g.A + item * g.sA;
+    float2 *C = g.C + item * g.sC;
+    for (int64_t m = (int64_t)blockIdx.x * G_THREADS + threadIdx.x; m < M;
+         m += (int64_t)gridDim.x * G_THREADS) {
+        float2 x[K];
+        if (K % 2 == 0 && vec_a) {
+            const float4 *a4 = reinterpret_cast<const float4 *>(A + m * K);
+#pragma unroll
+            for (int j = 0; j < K / 2; ++j) {
+                const float4 v = a4[j];
+                x[2 * j] = make_float2(v.x, v.y);
+                x[2 * j + 1] = make_float2(v.z, v.w);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < K; ++j) x[j] = A[m * K + j];
+        }
+        float2 y[N];
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) cfma(a, x[kk], Bs[kk * N + c]);
+            y[c] = a;
+        }
+        if (N % 2 == 0 && vec_c) {
+            float4 *c4 = reinterpret_cast<float4 *>(C + m * N);
+#pragma unroll
+            for (int j = 0; j < N / 2; ++j) c4[j] = make_float4(y[2 * j].x, y[2 * j].y, y[2 * j + 1].x, y[2 * j + 1].y);
+        } else {
+#pragma unroll
+            for (int c = 0; c < N; ++c) C[m * N + c] = y[c];
+        }
+    }
+}
+
+template <int K>
+static void launch_rows_n(int N, dim3 grid, const GemmItemSrc &g, int64_t M, int va, int vc,
+                          cudaStream_t st) {
+    switch (N) {
+        case 1: cgemm_rows_kernel<K, 1><<<grid, G_THREADS, 0, st>>>(g, M, va, vc); break;
+        case 2: cgemm_rows_kernel<K, 2><<<grid, G_THREADS, 0, st>>>(g, M, va, vc); break;
+        case 4: cgemm_rows_kernel<K, 4><<<grid, G_THREADS, 0, st>>>(g, M, va, vc); break;
+        default: cgemm_rows_kernel<K, 8><<<grid, G_THREADS, 0, st>>>(g, M, va, vc); break;
+    }
+}
+
+static bool pow2_upto8(int64_t x) { return x == 1 || x == 2 || x == 4 || x == 8; }
+
 static cudaError_t run_simt_gemm(const GemmItemSrc &g, int64_t M, int64_t K, int64_t N,
                                  int64_t batch, cudaStream_t st) {
     if (K <= 0 || N <= 0 || M <= 0 || batch <= 0) return cudaSuccess;
     if (batch > 65535) return cudaErrorInvalidValue;
+    if (pow2_upto8(K) && pow2_upto8(N)) {
+        // 16-byte vector access needs 16-byte aligned rows and item bases
+        auto al16 = [](const void *p) { return ((uintptr_t)p & 15) == 0; };
+        const int va = al16(g.A) && (K % 2 == 0) && (g.sA % 2 == 0);
+        const int vc = al16(g.C) && (N % 2 == 0) && (g.sC % 2 == 0);
+        const int64_t blocks = std::min<int64_t>((M + G_THREADS - 1) / G_THREADS, (int64_t)1 << 20);
+        dim3 grid((unsigned)blocks, (unsigned)batch, 1);
+        switch (K) {
+            case 1: launch_rows_n<1>((int)N, grid, g, M, va, vc, st); break;
+            case 2: launch_rows_n<2>((int)N, grid, g, M, va, vc, st); break;
+            case 4: launch_rows_n<4>((int)N, grid, g, M, va, vc, st); break;
+            default: launch_rows_n<8>((int)N, grid, g, M, va, vc, st); break;
+        }
+        return cudaGetLastError();
+    }
     const int BN = (int)std::min<int64_t>(N, 256);
     const int BM = std::min(4096 / BN, 512);
     const int64_t gx = (M + BM - 1) / BM;
@@ -865,6 +950,58 @@ cudaError_t launch_xeb_sum(const double2 *amps, int64_t n, double *out_sum, cuda
     xeb_partial_kernel<<<nb, 256, 0, st>>>(amps, n, out_sum + 1);
     xeb_final_kernel<<<1, 1, 0, st>>>(out_sum + 1, nb, out_sum);
     return cudaGetLastError();
+}
+
+// --------------------------------------------------- FP32 FMA peak probe
+// Independent FMA chains, enough per thread and enough threads per SM that
+// the FP32 pipes never wait on a result: the rate this GPU reaches on plain
+// FP32 FMAs (the arithmetic the fused stem pass runs on). Each thread keeps
+// FMA_CHAINS accumulators and runs FMA_ITERS rounds; the sum goes to out
+// only if it equals a value it cannot reach, which keeps the work live.
+constexpr int FMA_CHAINS = 16;
+constexpr int FMA_ITERS = 16384;
+__global__ void __launch_bounds__(256) fma_peak_kernel(float seed, float *out) {
+    float a[FMA_CHAINS];
+#pragma unroll
+    for (int i = 0; i < FMA_CHAINS; ++i) a[i] = seed + (float)(threadIdx.x + i);
+    const float b = 0.999999f, c = 1e-7f;
+    for (int it = 0; it < FMA_ITERS; ++it) {
+#pragma unroll
+        for (int i = 0; i < FMA_CHAINS; ++i) a[i] = fmaf(a[i], b, c);
+    }
+    float t = 0.f;
+#pragma unroll
+    for (int i = 0; i < FMA_CHAINS; ++i) t += a[i];
+    if (t == -1.2345e30f) out[blockIdx.x] = t;
+}
+
+cudaError_t measure_fma_peak(cudaStream_t st, double *tflops, int *sm_count) {
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int blocks = sms * 8;  // 8 blocks of 256 threads per SM: 64 warps
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    float best = 1e30f;
+    for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {  // first launch warms up
+        cudaEventRecord(e0, st);
+        fma_peak_kernel<<<blocks, 256, 0, st>>>(1.0f, nullptr);
+        cudaEventRecord(e1, st);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0 && e == cudaSuccess) best = std::min(best, ms);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) return e;
+    const double flops = 2.0 * FMA_CHAINS * (double)FMA_ITERS * 256.0 * blocks;
+    *tflops = flops / (best * 1e-3) / 1e12;
+    *sm_count = sms;
+    return cudaSuccess;
 }
 
 // ------------------------------------------------------- frugal sampling

@@ -100,6 +100,10 @@ cudaError_t launch_frugal_sample(const double2 *amps, const double *u, const dou
                                  int K, int n_qubits, double M, int32_t *idx, int32_t *cnt,
                                  double2 *picked, cudaStream_t st);
 
+// FP32 FMA rate of this GPU (TFLOP/s) from independent FMA chains on every
+// SM, best of three timed launches; synchronises st.
+cudaError_t measure_fma_peak(cudaStream_t st, double *tflops, int *sm_count);
+
 bool tc_gemm_supported(int k, int n);
 cudaError_t tc_gemm_init();
 cudaError_t tc_error_flag(int *out);

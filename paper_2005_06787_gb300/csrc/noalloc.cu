@@ -74,7 +74,9 @@ __global__ void noalloc_begin_kernel(NoAllocScratch *s, int64_t s0, int64_t s1, 
 
 void plan_contract_noalloc(Plan &p, uint64_t s0, uint64_t s1, cudaStream_t st, double *amps_out,
                            int accumulate) {
-    if (!p.prepared) fail(TN_ERR_INVALID_ARG, "plan not prepared (call tn_plan_prepare)");
+    // the plan's buffers live on the device it was prepared on, and the
+    // scratch address below is that of the current device: they must agree
+    require_plan_device(p);
     const int nsl = (int)p.scheme.sliced_list.size();
     const uint64_t total = nsl >= 63 ? ~0ull : (1ull << nsl);
     if (s0 > s1 || s1 > total) fail(TN_ERR_INVALID_ARG, "slice range outside [0, 2^n_sliced]");

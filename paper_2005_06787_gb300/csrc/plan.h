@@ -63,6 +63,7 @@ struct Plan {
 
     // device resources
     bool prepared = false;
+    int device = -1;            // CUDA device the plan was prepared on
     int n_prefix = 0;
     int SB = 1;                 // slices per fused batch
     float2 *d_pool = nullptr;   // branch storage
@@ -84,6 +85,9 @@ struct Plan {
 };
 
 void plan_prepare(Plan &p, const uint8_t *prefixes, int n_prefixes, cudaStream_t st);
+// Fails with TN_ERR_INVALID_ARG unless the plan is prepared and the current
+// device is the one it was prepared on (its buffers live there).
+void require_plan_device(const Plan &p);
 std::vector<tn_launch_record> plan_profile(Plan &p, uint64_t s0, tn_precision prec,
                                           tn_exec_mode mode, cudaStream_t st);
 void plan_contract_noalloc(Plan &p, uint64_t s0, uint64_t s1, cudaStream_t st, double *amps_out,

@@ -483,24 +483,29 @@ def test_full_size_plan_identity_fsim_closed_form(name, n_open, extra):
 
 
 # ------------------------------- full size, real gates, stored oracle slices
-# tests/golden/diag53_m12_slices.json holds FP64 oracle values of slices 0 and
-# 1 of the 53-qubit, 12-cycle workload (written by make_diag53_m12_slices.py
-# from the order and sliced wire segments in diag53_m12_scheme.json). The plan
-# is rebuilt from that order and those segments, so the comparison is always
-# on the same sub-networks.
+# tests/golden/<workload>_slices.json holds FP64 oracle values of slices 0
+# and 1 of the 53-qubit 12- and 14-cycle workloads (written by
+# make_stored_slices.py from the order and sliced wire segments in
+# <workload>_scheme.json, which make_scheme.py exports from the planner). The
+# plan is rebuilt from that order and those segments, so the comparison is
+# always on the same sub-networks.
 
-def _stored_m12_plan(**kw):
+def _stored_plan(name, **kw):
     from bench import workload_inputs
-    sch = json.load(open(os.path.join(GOLD, "diag53_m12_scheme.json")))
-    gold = json.load(open(os.path.join(GOLD, "diag53_m12_slices.json")))
+    sch = json.load(open(os.path.join(GOLD, f"{name}_scheme.json")))
+    gold = json.load(open(os.path.join(GOLD, f"{name}_slices.json")))
     assert gold["sliced_wires"] == sch["sliced_wires"]
-    c, oq, cb = workload_inputs("diag53_m12")
+    c, oq, cb = workload_inputs(name)
     net = P.tn_build_network(c, oq, cb)
     _, _, q, s = net.info()
     eid = {(int(a), int(b)): e for e, (a, b) in enumerate(zip(q, s))}
     sliced = [eid[tuple(w)] for w in sch["sliced_wires"]]
     plan = P.tn_plan_create(net, order=[tuple(x) for x in sch["order"]], sliced_edges=sliced, **kw)
     return plan, gold
+
+
+def _stored_m12_plan(**kw):
+    return _stored_plan("diag53_m12", **kw)
 
 
 @pytest.mark.parametrize("mode", ["fused", "plain"])
@@ -532,5 +537,44 @@ def test_diag53_m12_merged_gemm_steps_per_precision(prec, capsys):
     # shared one accumulator, whose truncating FP32 adds biased every step).
     # 3xBF16 carries about 16 significand bits per operand (hi + lo), so its
     # error is reported and bounded, as is the single BF16 product's.
+    tol = {"fp32": TOL, "tf32x3": TOL, "bf16x3": 1e-4, "bf16x1": 0.1}[prec]
+    assert max(errs) < tol
+
+
+# The bench workload (53 qubits, 14 cycles, cw 30: stem tensors of 2^30
+# entries) with real gates, in the bench's launch configuration (tile 12, up
+# to 8 steps per pass, one slice per launch), against the stored FP64 oracle
+# slices, element by element.
+@pytest.mark.parametrize("extra", [{"tile_bits": 12, "max_pass_steps": 8}, {}])
+def test_diag53_m14_slices_match_stored_oracle(extra, capsys):
+    plan, gold = _stored_plan("diag53_m14", **extra)
+    P.tn_plan_prepare(plan)
+    info = P.tn_plan_info(plan)
+    assert info["cw"] == 30 and info["n_gemm_steps"] == 0
+    errs = []
+    for sid, v in gold["slices"].items():
+        ref = np.asarray(v["re"]) + 1j * np.asarray(v["im"])
+        got = run(plan, int(sid), int(sid) + 1)[0]
+        errs.append(rel_l2(got, ref))
+    with capsys.disabled():
+        print(f"\ndiag53_m14 {extra or 'planner defaults'}: rel L2 vs FP64 oracle per slice {errs}")
+    assert max(errs) < TOL
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3", "bf16x3", "bf16x1"])
+def test_diag53_m14_merged_gemm_steps_per_precision(prec, capsys):
+    # the bench's precision sweep plan: runs of 3 branches merged, every stem
+    # step a GEMM step; FP32-accurate paths gated at 1e-5 (reading of the
+    # tolerance: FP32 SIMT and 3xTF32), the BF16 ones bounded
+    plan, gold = _stored_plan("diag53_m14", merge_group=3)
+    assert P.tn_plan_info(plan)["n_gemm_steps"] > 60
+    P.tn_plan_prepare(plan)
+    errs = []
+    for sid, v in gold["slices"].items():
+        ref = np.asarray(v["re"]) + 1j * np.asarray(v["im"])
+        got = run(plan, int(sid), int(sid) + 1, prec=prec)[0]
+        errs.append(rel_l2(got, ref))
+    with capsys.disabled():
+        print(f"\ndiag53_m14 merged, {prec}: rel L2 vs FP64 oracle per slice {errs}")
     tol = {"fp32": TOL, "tf32x3": TOL, "bf16x3": 1e-4, "bf16x1": 0.1}[prec]
     assert max(errs) < tol
