@@ -92,7 +92,7 @@ def test_noalloc_rejects_oversize_plan_and_host_output():
 # After a first call has loaded every kernel, further calls must leave the
 # device's free memory unchanged: the call allocates nothing.
 CASES = {
-    "shrink": dict(grid=(4, 5), cycles=10, seed=72, opts=dict(cw_limit=14, restarts=2, min_sliced=10,
+    "shrink": dict(grid=(4, 5), cycles=12, seed=72, opts=dict(cw_limit=14, restarts=2, min_sliced=8,
                                                                slice_batch=1024)),
     "cbank": dict(grid=(3, 4), cycles=8, seed=71, opts=dict(cw_limit=7, restarts=3, min_sliced=3,
                                                              slice_batch=1)),
