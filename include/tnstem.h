@@ -368,7 +368,14 @@ tn_status tn_permute(const float *in, float *out, int32_t rank, const int32_t *p
 
 /* Complex GEMM C[b][m][n] = sum_k A[b][m][k] * B[b][k][n], row-major, batch
  * strides in complex elements (0 broadcasts). One stem step, Supp. A.1
- * (a pairwise contraction is a GEMM after permutation). */
+ * (a pairwise contraction is a GEMM after permutation); large K and N are the
+ * steps that absorb merged branches (Supp. A.3 "Branch merging"). FP32 runs
+ * on the CUDA cores; the tensor-core precisions on tcgen05, with a
+ * TMA-pipelined kernel when K >= 32, 2N is a multiple of 128 (x3) or 256
+ * (BF16 x1), M >= 128 and A, C are 16-byte aligned (it allocates a
+ * stream-ordered workspace of 2 x 2N x 2K operand elements for the split B).
+ * Asynchronous on cuda_stream: a tensor-core wait that gave up is reported by
+ * tn_device_status. */
 tn_status tn_cgemm(const float *A, const float *B, float *C, int64_t M, int64_t K, int64_t N,
                    int64_t batch, int64_t strideA, int64_t strideB, int64_t strideC,
                    tn_precision prec, void *cuda_stream);

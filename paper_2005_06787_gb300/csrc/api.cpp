@@ -498,12 +498,6 @@ tn_status tn_cgemm(const float *A, const float *B, float *C, int64_t M, int64_t 
         TN_CUDA(tn::launch_cgemm(reinterpret_cast<const float2 *>(A), reinterpret_cast<const float2 *>(B),
                                  reinterpret_cast<float2 *>(C), M, K, N, batch, strideA, strideB,
                                  strideC, prec, (cudaStream_t)cuda_stream));
-        if (prec != TN_PREC_FP32_SIMT) {
-            TN_CUDA(cudaStreamSynchronize((cudaStream_t)cuda_stream));
-            int flag = 0;
-            TN_CUDA(tn::tc_error_flag(&flag));
-            if (flag) tn::fail(TN_ERR_TIMEOUT, "tensor-core GEMM wait timed out");
-        }
     });
 }
 

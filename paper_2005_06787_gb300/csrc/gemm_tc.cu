@@ -679,6 +679,18 @@ cudaError_t launch_tc_cgemm(const float2 *A, const float2 *B, float2 *C, int64_t
                             int64_t N, int64_t batch, int64_t sA, int64_t sB, int64_t sC,
                             tn_precision prec, cudaStream_t st) {
     if (K > (1 << 20) || N > (1 << 20)) return cudaErrorInvalidValue;
+    // large K and N: the TMA-fed pipelined kernel, one launch per batch item
+    bool large = g_tc_err != nullptr && batch >= 1;
+    for (int64_t b = 0; b < batch && large; ++b)
+        large = tc_large_supported(M, K, N, prec, A + b * sA, C + b * sC);
+    if (large) {
+        for (int64_t b = 0; b < batch; ++b) {
+            cudaError_t e = launch_tc_cgemm_large(A + b * sA, B + b * sB, C + b * sC, M, K, N, prec,
+                                                  g_tc_err, st);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
     TcArgs a{};
     a.A = reinterpret_cast<const float *>(A);
     a.B = reinterpret_cast<const float *>(B);

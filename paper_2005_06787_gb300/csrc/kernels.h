@@ -104,6 +104,13 @@ cudaError_t launch_frugal_sample(const double2 *amps, const double *u, const dou
 // SM, best of three timed launches; synchronises st.
 cudaError_t measure_fma_peak(cudaStream_t st, double *tflops, int *sm_count);
 
+// Large complex GEMMs on tcgen05 (gemm_large.cu): TMA-fed, warp-specialised,
+// for K >= 32, 2K % 64 == 0, 2N a multiple of the tile width (128 for the x3
+// precisions, 256 for BF16 x1), M >= 128 and 16-byte aligned A and C.
+bool tc_large_supported(int64_t M, int64_t K, int64_t N, tn_precision prec, const void *A, const void *C);
+cudaError_t launch_tc_cgemm_large(const float2 *A, const float2 *B, float2 *C, int64_t M, int64_t K,
+                                  int64_t N, tn_precision prec, int *err, cudaStream_t st);
+
 bool tc_gemm_supported(int k, int n);
 cudaError_t tc_gemm_init();
 cudaError_t tc_error_flag(int *out);

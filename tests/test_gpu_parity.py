@@ -121,6 +121,29 @@ def test_cgemm_tensor_core_matches_fp64(prec, M, K, N, batch):
     assert rel_l2(got, ref) < TC_TOL[prec], rel_l2(got, ref)
 
 
+# Shapes of the TMA-pipelined tcgen05 kernel (K >= 32 and 2N a multiple of its
+# tile width: 128 for x3, 256 for BF16 x1), including ragged M (partial last
+# tile, rows past M read as zero and not stored), batches (one launch per
+# item) and the large benchmark shape, whose reference is checked on sampled
+# rows (every row must be written: C starts as NaN).
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3", "bf16x1"])
+@pytest.mark.parametrize("M,K,N,batch", [(128, 32, 128, 1), (1000, 64, 128, 1), (130, 32, 256, 2),
+                                         (4096, 256, 64, 1), (2048, 128, 512, 1), (16384, 512, 512, 1)])
+def test_cgemm_large_tensor_core_matches_fp64(prec, M, K, N, batch):
+    A = random_complex((batch, M, K), 31, np.complex64)
+    B = random_complex((batch, K, N), 32, np.complex64)
+    dA = torch.from_numpy(A.view(np.float32).copy()).cuda()
+    dB = torch.from_numpy(B.view(np.float32).copy()).cuda()
+    dC = torch.full((batch * M * N * 2,), float("nan"), dtype=torch.float32, device="cuda")
+    P.tn_cgemm(dA, dB, dC, M, K, N, batch, M * K, K * N, M * N, prec=prec)
+    torch.cuda.synchronize()
+    got = dC.cpu().numpy().view(np.complex64).reshape(batch, M, N)
+    assert np.isfinite(got.view(np.float32)).all()
+    rows = np.arange(M) if M <= 4096 else np.unique(np.r_[0, M - 1, np.random.default_rng(3).integers(0, M, 512)])
+    ref = np.matmul(A[:, rows].astype(np.complex128), B.astype(np.complex128))
+    assert rel_l2(got[:, rows], ref) < TC_TOL[prec], rel_l2(got[:, rows], ref)
+
+
 @pytest.mark.parametrize("prec,tol", [("fp32", TOL), ("tf32x3", TOL), ("bf16x3", 1e-4)])
 def test_cgemm_chain_of_61_unitary_steps(prec, tol, capsys):
     # 61 stem-like GEMM steps (4 x 4 complex unitaries, magnitudes kept) applied
