@@ -318,6 +318,53 @@ def sampling_run(stream, job_seconds: float, n_open: int, M: float = 10.0):
             "porter_thomas_accept_per_batch": p_batch}
 
 
+def gemm_large_run(stream, peaks, shapes=((16384, 512, 512), (16384, 1024, 1024))):
+    """tn_cgemm on large complex shapes (Supp. A.3: merged branches make stem
+    steps dense GEMMs) per precision: the TMA-pipelined tcgen05 kernel for the
+    tensor-core precisions, the SIMT kernel for FP32. Executed flops count 3
+    products for the x3 precisions; the peak is the measured BF16 one (x0.5
+    for TF32). Each call includes its B split and workspace; inputs resident,
+    CUDA events around 20 back-to-back calls; error on 64 sampled rows against
+    an FP64 product of the same FP32 inputs."""
+    import torch
+    import paper_2005_06787_gb300 as P
+    out = []
+    rng = np.random.default_rng(17)
+    for (M, K, N) in shapes:
+        A = torch.randn(2 * M * K, device="cuda")
+        B = torch.randn(2 * K * N, device="cuda") / math.sqrt(K)
+        C = torch.empty(2 * M * N, device="cuda")
+        rows = rng.integers(0, M, 64)
+        a = A.view(-1, 2 * K).cpu().numpy()[rows].view(np.complex64).astype(np.complex128)
+        b = B.cpu().numpy().view(np.complex64).reshape(K, N).astype(np.complex128)
+        ref = a @ b
+        for prec in ("tf32x3", "bf16x3", "bf16x1", "fp32"):
+            reps = 20 if prec != "fp32" else 3
+            P.tn_cgemm(A, B, C, M, K, N, prec=prec, stream=stream)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                P.tn_cgemm(A, B, C, M, K, N, prec=prec, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            got = C.view(-1, 2 * N).cpu().numpy()[rows].view(np.complex64).astype(np.complex128)
+            alg = 8.0 * M * K * N
+            mult = 3 if prec in ("tf32x3", "bf16x3") else 1
+            peak = peaks["bf16_tflops"] * (0.5 if prec == "tf32x3" else 1.0)
+            exe = mult * alg / (ms * 1e-3) / 1e12
+            out.append({"M": M, "K": K, "N": N, "prec": prec, "ms_per_call": ms,
+                        "alg_tflops": alg / (ms * 1e-3) / 1e12, "exec_tflops": exe,
+                        "exec_frac_of_tensor_peak": exe / peak if prec != "fp32" else None,
+                        "rel_l2_vs_fp64": float(np.linalg.norm(got - ref) / np.linalg.norm(ref))})
+        del A, B, C
+        torch.cuda.empty_cache()
+    P.tn_device_status()
+    return {"peak_bf16_tflops": peaks["bf16_tflops"], "peak_note": "measured BF16 burst; TF32 = 0.5 x",
+            "rows": out}
+
+
 def run_reference(args):
     """The oracle arm: the FP64 CPU oracle on bounded samples of the same
     workload (each step one bounded sample: the heaviest stem steps of slice
@@ -883,6 +930,9 @@ def main():
     # passes, GEMM steps, accumulate, advance, finalize, and one staging
     # kernel before each pass that reads its branch matrices from the constant bank
     launches_per_step = (info["n_passes_fused"] + info["n_gemm_steps"] + 2) + 1 + info["n_passes_cbank"]
+    gemm_large = None
+    if rank == 0 and not args.no_sweep:
+        gemm_large = gemm_large_run(stream, measured_peaks()[0])
     samp = None
     if rank == 0 and not args.no_sampling:
         samp = sampling_run(stream, 2 ** info["n_sliced"] / slices_per_s, len(oq))
@@ -918,6 +968,7 @@ def main():
             "cpu_baseline": cpu,
             "parity": parity,
             "precision_sweep": sweep,
+            "tn_cgemm_large": gemm_large,
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks,
             "amp_norm_check": float(np.linalg.norm(amps)),

@@ -142,3 +142,66 @@ def test_learned_search_gain_diag53_m12(capsys):
               f"{rho_mlp:.2f}); plain model {np.round(p_flop, 2).tolist()} (mean |log err| "
               f"{err_flop:.3f}, rank corr {rho_flop:.2f})")
     assert err_mlp < err_flop
+
+
+def _stored_scheme_plan(name, **kw):
+    """Plan of a workload rebuilt from its stored order and sliced wire
+    segments (tests/golden), with other launch options."""
+    import json
+    import os
+    from bench import plan_options, workload_inputs
+    gold = os.path.join(os.path.dirname(__file__), "golden")
+    sch = json.load(open(os.path.join(gold, f"{name}_scheme.json")))
+    c, oq, cb = workload_inputs(name)
+    net = P.tn_build_network(c, oq, cb)
+    _, _, q, s = net.info()
+    eid = {(int(a), int(b)): e for e, (a, b) in enumerate(zip(q, s))}
+    return P.tn_plan_create(net, order=[tuple(x) for x in sch["order"]],
+                            sliced_edges=[eid[tuple(w)] for w in sch["sliced_wires"]],
+                            **dict(plan_options(name), **kw))
+
+
+def test_learned_pick_beats_plain_model_pick_diag53_m14(capsys):
+    # The network is trained on launch timings of the 53-qubit 12-cycle
+    # workload only; it then scores launch configurations (tile size x steps
+    # per pass) of the held-out 14-cycle bench workload beside the plain
+    # FLOP-and-memory model. Where the two picks differ, the learned pick must
+    # run strictly faster on the GPU; where they agree the gain is 1.
+    stream = torch.cuda.current_stream()
+    rows = []
+    for tb in (10, 11, 12):
+        for ms in (2, 4, 6, 8):
+            plan = _stored_scheme_plan("diag53_m12", tile_bits=tb, max_pass_steps=ms)
+            P.tn_plan_prepare(plan, stream=stream)
+            rows.append((plan, "fp32", "fused"))
+    X, y, _ = learned.gather(rows, repeats=2)
+    del rows
+    torch.cuda.empty_cache()
+    mlp = learned.train_cost_model(X, y, epochs=600)
+    cands = [(tb, ms) for tb in (11, 12) for ms in (2, 4, 6, 8)]
+    pm, pf = {}, {}
+    for cand in cands:
+        plan = _stored_scheme_plan("diag53_m14", tile_bits=cand[0], max_pass_steps=cand[1])
+        Xc, flop_ms = P.tn_plan_features(plan)
+        pm[cand] = float(np.exp(mlp.predict(Xc).astype(np.float64)).sum())
+        pf[cand] = float(flop_ms.sum())
+        del plan
+    pick_m = min(cands, key=lambda k: pm[k])
+    pick_f = min(cands, key=lambda k: pf[k])
+    measured = {}
+    for cand in {pick_m, pick_f}:
+        plan = _stored_scheme_plan("diag53_m14", tile_bits=cand[0], max_pass_steps=cand[1])
+        P.tn_plan_prepare(plan, stream=stream)
+        measured[cand] = _time_plan(plan, 3, stream)
+        del plan
+        torch.cuda.empty_cache()
+    gain = measured[pick_f] / measured[pick_m]
+    with capsys.disabled():
+        print(f"\ndiag53_m14 launch options (tile bits, steps per pass): learned pick {pick_m} "
+              f"(predicted {pm[pick_m]:.1f} ms/slice, measured {measured[pick_m]:.1f}), plain-model "
+              f"pick {pick_f} (predicted {pf[pick_f]:.1f} ms/slice, measured {measured[pick_f]:.1f}); "
+              f"measured gain {gain:.3f}x; trained on {len(y)} launches of diag53_m12")
+    if pick_m != pick_f:
+        assert gain > 1.0, (pick_m, pick_f, measured)
+    else:
+        assert gain == 1.0
