@@ -180,6 +180,17 @@ def test_cgemm_chain_of_61_unitary_steps(prec, tol, capsys):
     assert rel < tol
 
 
+def test_fp32_fma_peak_is_sane():
+    # the fused pass's roofline denominator: independent FMA chains on every
+    # SM; it must see every SM and land between a quarter of and just above
+    # the unit-count bound (SMs x 128 lanes x 2 flops x 2.07 GHz)
+    tflops, sms = P.tn_fp32_fma_peak()
+    props = torch.cuda.get_device_properties(0)
+    assert sms == props.multi_processor_count
+    nominal = sms * 128 * 2 * 2.07e9 / 1e12
+    assert 0.25 * nominal < tflops < 1.05 * nominal, (tflops, nominal)
+
+
 def test_linear_xeb_kernel():
     a = random_complex((4096,), 3) / 64.0
     d = torch.from_numpy(a.view(np.float64).copy()).cuda()
