@@ -14,8 +14,16 @@ Contents and the passages they follow:
 * ``build_network``: the circuit as a tensor network (Sec. 3, Supp. A.1):
   one tensor per |0>, gate and closed-qubit projector, one edge per wire
   segment, open edges on the open qubits' last segments.
+* ``build_hypernetwork``: the same circuit as a multi-hypergraph (Supp. A.1
+  defines networks as hypergraphs; Sec. 3 names hyperedges for diagonal gate
+  parts, after BIS+18). With theta = pi/2, fSim(pi/2, phi) is the wire swap
+  times diag(1, -i, -i, e^{-i phi}): each two-qubit gate becomes a rank-2
+  diagonal tensor on the two current wire indices, which the wires then
+  exchange; an index is created only by |0> and single-qubit gates.
 * ``contract``: sequential pairwise contraction (Sec. 3, Schroedinger method;
-  Supp. A.1 contraction trees) with ``orc_contract`` as each step; sliced
+  Supp. A.1 contraction trees) with ``orc_contract`` as each step: a step
+  keeps E*_AB, the edges of the pair that are open or held by another
+  remaining tensor (in a graph: the edges of exactly one of the two); sliced
   edges are fixed by indexing, and ``contract_sliced_sum`` sums subtasks
   (Supp. A.1, "Slicing").
 * ``feynman``: T_H[b] as the literal sum of path values (Supp. A.1).
@@ -223,6 +231,52 @@ def build_network(circuit, open_qubits: Sequence[int], closed_bits: Sequence[int
     return Network(tensors, edges, open_edges, kinds)
 
 
+def build_hypernetwork(circuit, open_qubits: Sequence[int], closed_bits: Sequence[int]) -> Network:
+    """The circuit's hypergraph network (Supp. A.1, Sec. 3): indices are
+    created by |0> and single-qubit gates only; each fSim(pi/2, phi) is the
+    rank-2 tensor d[x_a, x_b] = fSim[(x_b, x_a), (x_a, x_b)] on the two
+    current wire indices, after which qubits a and b carry each other's
+    index. Index (q, j) is the one qubit q's j-th gate created ((q, 0): its
+    |0>). Raises ValueError unless theta = pi/2."""
+    n, m = circuit.n_qubits, circuit.n_cycles
+    if abs(np.cos(circuit.theta)) > 1e-12:
+        raise ValueError("hyperedge network needs fSim(pi/2, phi): a wire swap times a diagonal gate")
+    open_set = set(open_qubits)
+    closed = [q for q in range(n) if q not in open_set]
+    if len(closed) != len(closed_bits):
+        raise ValueError("closed_bits must give one bit per closed qubit")
+    cur: List[Edge] = [(q, 0) for q in range(n)]
+    made = [0] * n
+    tensors: List[np.ndarray] = []
+    edges: List[List[Edge]] = []
+    kinds: List[str] = []
+
+    def add(t, el, kind):
+        tensors.append(np.ascontiguousarray(t, dtype=np.complex128))
+        edges.append(el)
+        kinds.append(kind)
+
+    for q in range(n):
+        add(np.array([1.0, 0.0]), [cur[q]], "zero")
+    F = fsim(circuit.theta, circuit.phi).reshape(2, 2, 2, 2)  # [ya, yb, xa, xb]
+    D = np.array([[F[xb, xa, xa, xb] for xb in range(2)] for xa in range(2)])
+    for t in range(m + 1):
+        for q in range(n):
+            G = gate_1q(circuit.gates_1q[t][q])
+            made[q] += 1
+            out = (q, made[q])
+            add(G.T.copy(), [cur[q], out], "1q")  # T[in, out] = G[out, in]
+            cur[q] = out
+        if t == m:
+            break
+        for (qa, qb) in circuit.pairs[t]:
+            add(D, [cur[qa], cur[qb]], "diag")
+            cur[qa], cur[qb] = cur[qb], cur[qa]
+    for q, v in zip(closed, closed_bits):
+        add(np.array([1.0, 0.0]) if int(v) == 0 else np.array([0.0, 1.0]), [cur[q]], "proj")
+    return Network(tensors, edges, [cur[q] for q in open_qubits], kinds)
+
+
 def fix_edges(net: Network, sliced: Dict[Edge, int]) -> Network:
     """Sub-network with each sliced edge fixed to its value (Supp. A.1)."""
     tensors, edges = [], []
@@ -248,12 +302,18 @@ def _i64_labels(el: Sequence[Edge]) -> np.ndarray:
 
 
 def contract_pair(A: np.ndarray, ea: List[Edge], B: np.ndarray, eb: List[Edge],
-                  keep: Sequence[Edge] = ()) -> Tuple[np.ndarray, List[Edge]]:
-    """Contract A and B over their shared edges; output edges are A's
-    unshared edges then B's, in their own order."""
+                  keep: Optional[Sequence[Edge]] = None) -> Tuple[np.ndarray, List[Edge]]:
+    """Contract A and B. Without ``keep`` (a graph): the shared edges are
+    summed and the output edges are A's unshared edges then B's. With
+    ``keep`` (E*_AB of Supp. A.1): the output edges are the edges of A, then
+    those of B not in A, that are in ``keep``; every other edge is summed."""
     sb = set(eb)
     sa = set(ea)
-    ec = [e for e in ea if e not in sb] + [e for e in eb if e not in sa]
+    if keep is None:
+        ec = [e for e in ea if e not in sb] + [e for e in eb if e not in sa]
+    else:
+        kp = set(keep)
+        ec = [e for e in ea if e in kp] + [e for e in eb if e in kp and e not in sa]
     C = np.zeros(1 << len(ec), dtype=np.complex128)
     A1 = np.ascontiguousarray(A.reshape(-1))
     B1 = np.ascontiguousarray(B.reshape(-1))
@@ -283,12 +343,17 @@ def contract(net: Network, order: Optional[Sequence[Tuple[int, int]]] = None,
             order.append((cur, i))
             cur = N + i - 1
     nid = N
+    opn = set(net.open_edges)
     for (a, b) in order:
         if a not in live or b not in live or a == b:
             raise ValueError(f"invalid contraction pair ({a}, {b})")
         A, ea = live.pop(a)
         B, eb = live.pop(b)
-        C, ec = contract_pair(A, ea, B, eb)
+        # E*_AB: the pair's edges that are open or held by a remaining tensor
+        held = set(opn)
+        for _, el in live.values():
+            held.update(el)
+        C, ec = contract_pair(A, ea, B, eb, keep=[e for e in set(ea) | set(eb) if e in held])
         live[nid] = (C, ec)
         nid += 1
     if len(live) != 1:

@@ -12,8 +12,10 @@
  *                              segments, which is what fixing a sliced edge
  *                              means, Supp. A.1 "Slicing").
  *   orc_contract            -- one pairwise contraction step, Supp. A.1: the
- *                              sum over the shared edges of the product of
- *                              entries, for every assignment of the others.
+ *                              sum over the edges of E_AB outside E*_AB of
+ *                              the product of entries, for every assignment
+ *                              of the output edges E*_AB (shared edges that
+ *                              stay in E*_AB, hyperedges, are not summed).
  *   orc_feynman             -- the tensor-network value T_H[b] of Supp. A.1 as
  *                              the literal sum of Feynman path values F(a).
  *
@@ -172,12 +174,17 @@ static int find_edge(const int64_t *e, int r, int64_t x)
 }
 
 /*
- * One pairwise contraction step (Supp. A.1, "Contraction trees"):
- *   C[b] = sum over assignments c of the edges shared by A and B of
+ * One pairwise contraction step (Supp. A.1, "Contraction trees"): the step
+ * enumerates the assignments of E_AB, the edges of A or B, and sums the
+ * products of entries of those that agree on E*_AB, the output edges:
+ *   C[b] = sum over assignments c of the edges in E_AB but not in E*_AB of
  *          A[(b, c) restricted to A's edges] * B[(b, c) restricted to B's].
- * The output edge list ec must hold exactly the edges that belong to one of
- * A, B but not both. Returns 0, or -1 when the edge lists do not fit that
- * rule (a repeated edge, an output edge in both or neither input).
+ * In a graph an edge of both A and B is summed and every other edge is an
+ * output edge; in a hypergraph an edge of both A and B that other tensors
+ * (or the open edges) still hold is an output edge, taken at the same value
+ * in A and B and not summed. ec must list distinct edges of A or B. Returns
+ * 0, or -1 when the edge lists do not fit (a repeated edge, an output edge in
+ * neither input, more than 30 summed edges).
  */
 int orc_contract(const cplx *A, int ra, const int64_t *ea,
                  const cplx *B, int rb, const int64_t *eb,
@@ -190,16 +197,15 @@ int orc_contract(const cplx *A, int ra, const int64_t *ea,
         if (find_edge(eb, i, eb[i]) >= 0) return -1;
     for (int i = 0; i < rc; ++i)
         if (find_edge(ec, i, ec[i]) >= 0) return -1;
-    /* shared edges are summed; every other input edge must be an output edge */
-    int64_t shared[80];
+    for (int i = 0; i < rc; ++i)
+        if (find_edge(ea, ra, ec[i]) < 0 && find_edge(eb, rb, ec[i]) < 0) return -1;
+    /* summed edges: the edges of A or B that are not output edges */
+    int64_t summed[80];
     int k = 0;
     for (int i = 0; i < ra; ++i)
-        if (find_edge(eb, rb, ea[i]) >= 0) shared[k++] = ea[i];
-    for (int i = 0; i < rc; ++i) {
-        int inA = find_edge(ea, ra, ec[i]) >= 0, inB = find_edge(eb, rb, ec[i]) >= 0;
-        if (inA == inB) return -1;
-    }
-    if (ra + rb - 2 * k != rc) return -1;
+        if (find_edge(ec, rc, ea[i]) < 0) summed[k++] = ea[i];
+    for (int i = 0; i < rb; ++i)
+        if (find_edge(ec, rc, eb[i]) < 0 && find_edge(ea, ra, eb[i]) < 0) summed[k++] = eb[i];
     if (k > 30) return -1;
 
     /* stride of each output bit inside A and inside B (0 if absent) */
@@ -217,8 +223,9 @@ int orc_contract(const cplx *A, int ra, const int64_t *ea,
         int64_t oa = 0, ob = 0;
         for (int j = 0; j < k; ++j) {
             if (!((c >> (k - 1 - j)) & 1)) continue;
-            oa += (int64_t)1 << (ra - 1 - find_edge(ea, ra, shared[j]));
-            ob += (int64_t)1 << (rb - 1 - find_edge(eb, rb, shared[j]));
+            int ja = find_edge(ea, ra, summed[j]), jb = find_edge(eb, rb, summed[j]);
+            if (ja >= 0) oa += (int64_t)1 << (ra - 1 - ja);
+            if (jb >= 0) ob += (int64_t)1 << (rb - 1 - jb);
         }
         offA[c] = oa;
         offB[c] = ob;

@@ -21,17 +21,18 @@ import paper_2005_06787_gb300 as P  # noqa: E402
 from bench import plan_options, workload_inputs  # noqa: E402
 
 
-def main(name: str):
+def main(name: str, extra: dict):
     c, oq, cb = workload_inputs(name)
     net = P.tn_build_network(c, oq, cb)
     t = time.time()
-    plan = P.tn_plan_create(net, **plan_options(name))
+    plan = P.tn_plan_create(net, **dict(plan_options(name), **extra))
     order, sl = P.tn_plan_export(plan)
     info = P.tn_plan_info(plan)
     _, _, q, s = net.info()
     out = {"workload": name,
            "note": "contraction order and sliced wire segments of the library's plan for this "
                    "workload (plan_options in bench.py); schedule input for the oracle",
+           "planner_options_beyond_plan_options": extra,
            "log2_tc": info["log2_tc"], "cw": info["cw"], "n_sliced": info["n_sliced"],
            "order": [[int(a), int(b)] for a, b in order],
            "sliced_wires": [[int(q[e]), int(s[e])] for e in sl]}
@@ -42,4 +43,9 @@ def main(name: str):
 
 
 if __name__ == "__main__":
-    main(sys.argv[1] if len(sys.argv) > 1 else "diag53_m14")
+    # optional second argument: planner options beyond bench.plan_options, as
+    # JSON, e.g. the 20-cycle plan of total cost 2^62.09:
+    #   python make_scheme.py diag53_m20 '{"start_cluster": 148, "anneal_iters": 1200000,
+    #       "restarts": 1, "slice_restarts": 0, "max_sliced": 64}'
+    main(sys.argv[1] if len(sys.argv) > 1 else "diag53_m14",
+         json.loads(sys.argv[2]) if len(sys.argv) > 2 else {})

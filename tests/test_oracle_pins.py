@@ -410,3 +410,82 @@ def test_frugal_samples_xeb_near_one_on_deep_circuit():
     pu = np.abs(amps[np.arange(B), (key[:, 0] * 64).astype(int)]) ** 2
     assert abs(oracle.linear_xeb(pu, n)) < 0.2
 
+
+
+# ------------------------------------------- hyperedges (Supp. A.1, Sec. 3)
+# A network is a multi-hypergraph; with theta = pi/2, fSim is the wire swap
+# times diag(1, -i, -i, e^{-i phi}), so each two-qubit gate is a rank-2 tensor
+# on two hyperedges (oracle.build_hypernetwork). Pins: the pairwise step with
+# kept shared edges equals numpy's einsum; the hypergraph value equals the
+# state vector, the graph network's value and the Feynman sum; it does not
+# depend on the order; its slices add up; its index count has a closed form;
+# a planted wrong diagonal fails the state-vector pin.
+
+def test_contract_pair_with_kept_shared_edge_matches_einsum():
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((2, 2, 2)) + 1j * rng.standard_normal((2, 2, 2))
+    B = rng.standard_normal((2, 2, 2)) + 1j * rng.standard_normal((2, 2, 2))
+    # A[x, h, s], B[s, h, y]: h is kept (held elsewhere), s is summed
+    x, h, s_, y = (0, 0), (1, 0), (2, 0), (3, 0)
+    C, ec = oracle.contract_pair(A, [x, h, s_], B, [s_, h, y], keep=[x, h, y])
+    assert ec == [x, h, y]
+    np.testing.assert_allclose(C, np.einsum("xhs,shy->xhy", A, B), atol=1e-14)
+    # an edge of one input that is not kept is summed over that input alone
+    C2, ec2 = oracle.contract_pair(A, [x, h, s_], B, [s_, h, y], keep=[h])
+    np.testing.assert_allclose(C2, np.einsum("xhs,shy->h", A, B), atol=1e-13)
+
+
+def test_hypernetwork_index_count_closed_form():
+    # indices come from |0> and single-qubit gates only: n (m + 2)
+    c = random_circuit(grid_layout(3, 4), 6, 5)
+    net = oracle.build_hypernetwork(c, [0, 1], list(random_bits(10, 4)))
+    assert len(net.all_edges()) == c.n_qubits * (c.n_cycles + 2)
+    assert sum(k == "diag" for k in net.kinds) == sum(len(p) for p in c.pairs)
+    assert all(T.shape == (2, 2) for T, k in zip(net.tensors, net.kinds) if k == "diag")
+
+
+def test_hypernetwork_value_equals_feynman_sum():
+    c = random_circuit(grid_layout(2, 2), 2, 9)
+    net = oracle.build_hypernetwork(c, [1, 2], list(random_bits(2, 5)))
+    assert len(net.all_edges()) <= 30
+    np.testing.assert_allclose(oracle.contract(net), oracle.feynman(net), atol=1e-14)
+
+
+def test_hypernetwork_value_equals_statevector_and_graph_network():
+    for (r, cc, m, seed, n_open) in [(3, 3, 5, 21, 3), (4, 4, 8, 1, 0), (3, 4, 6, 8, 6)]:
+        c = random_circuit(grid_layout(r, cc), m, seed)
+        oq = list(range(n_open))
+        cb = list(random_bits(c.n_qubits - n_open, seed + 100))
+        hyp = oracle.contract(oracle.build_hypernetwork(c, oq, cb)).reshape(-1)
+        np.testing.assert_allclose(hyp, oracle.sv_amplitudes(c, oq, cb), atol=1e-13)
+        np.testing.assert_allclose(hyp, oracle.contract(oracle.build_network(c, oq, cb)).reshape(-1),
+                                   atol=1e-13)
+
+
+def test_hypernetwork_value_independent_of_order_and_slices_add_up():
+    c = random_circuit(grid_layout(2, 3), 4, 17)
+    net = oracle.build_hypernetwork(c, [0, 4], list(random_bits(4, 2)))
+    ref = oracle.contract(net)
+    rng = random.Random(7)
+    for _ in range(4):
+        np.testing.assert_allclose(oracle.contract(net, _random_order(len(net.tensors), rng)), ref,
+                                   atol=1e-13)
+    inner = [e for e in net.all_edges() if e not in net.open_edges and e[1] > 0]
+    sliced = inner[2:5]
+    np.testing.assert_allclose(oracle.contract_sliced_sum(net, sliced), ref, atol=1e-13)
+
+
+def test_hypernetwork_rejects_fsim_that_is_not_a_swap_times_diagonal():
+    c = random_circuit(grid_layout(2, 2), 2, 9, theta=1.2)
+    with pytest.raises(ValueError):
+        oracle.build_hypernetwork(c, [0], [0, 1, 1])
+
+
+def test_planted_wrong_phase_in_hyperedge_diagonal_fails_sv_pin(monkeypatch):
+    c = random_circuit(grid_layout(3, 3), 4, 23)
+    oq, cb = [0, 1], list(random_bits(7, 6))
+    sv = oracle.sv_amplitudes(c, oq, cb)
+    real = oracle.fsim
+    monkeypatch.setattr(oracle, "fsim", lambda th, ph: real(th, -ph))  # e^{+i phi}: wrong sign
+    hyp = oracle.contract(oracle.build_hypernetwork(c, oq, cb)).reshape(-1)
+    assert np.abs(hyp - sv).max() > 1e-3 * np.abs(sv).max()
