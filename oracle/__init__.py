@@ -344,16 +344,22 @@ def contract(net: Network, order: Optional[Sequence[Tuple[int, int]]] = None,
             cur = N + i - 1
     nid = N
     opn = set(net.open_edges)
+    holders: Dict[Edge, int] = {}  # number of remaining tensors holding each edge
+    for _, el in live.values():
+        for e in el:
+            holders[e] = holders.get(e, 0) + 1
     for (a, b) in order:
         if a not in live or b not in live or a == b:
             raise ValueError(f"invalid contraction pair ({a}, {b})")
         A, ea = live.pop(a)
         B, eb = live.pop(b)
+        for e in ea + eb:
+            holders[e] -= 1
         # E*_AB: the pair's edges that are open or held by a remaining tensor
-        held = set(opn)
-        for _, el in live.values():
-            held.update(el)
-        C, ec = contract_pair(A, ea, B, eb, keep=[e for e in set(ea) | set(eb) if e in held])
+        keep = [e for e in set(ea) | set(eb) if e in opn or holders[e] > 0]
+        C, ec = contract_pair(A, ea, B, eb, keep=keep)
+        for e in ec:
+            holders[e] += 1
         live[nid] = (C, ec)
         nid += 1
     if len(live) != 1:
