@@ -368,6 +368,60 @@ def gemm_large_run(stream, peaks, shapes=((16384, 512, 512), (16384, 1024, 1024)
             "rows": out}
 
 
+def twenty_cycle_run(stream, n_slices: int = 8):
+    """The 20-cycle workload on its best stored plan (total cost 2^62.09, 23
+    sliced edges, cw 30; tests/golden/diag53_m20_scheme.json) in the bench's
+    launch configuration: seeded slices timed, the whole 64-amplitude batch
+    extrapolated (Supp. A.4: per-subtask time x number of subtasks)."""
+    import torch
+    import paper_2005_06787_gb300 as P
+    from synthetic.circuits import SplitMix64
+    name = "diag53_m20"
+    sch = stored_scheme(name)
+    if sch is None:
+        return None
+    order, wires = sch
+    c, oq, cb = workload_inputs(name)
+    net = P.tn_build_network(c, oq, cb)
+    _, _, q, s = net.info()
+    eid = {(int(a), int(b)): e for e, (a, b) in enumerate(zip(q, s))}
+    plan = P.tn_plan_create(net, order=order, sliced_edges=[eid[w] for w in wires], cw_limit=30,
+                            tile_bits=12, max_pass_steps=8)
+    P.tn_plan_prepare(plan, stream=stream)
+    info = P.tn_plan_info(plan)
+    rng = SplitMix64(CONFIGS[name]["bit_seed"])
+    ids = [rng.next() % (1 << info["n_sliced"]) for _ in range(n_slices)]
+    out = torch.zeros(2 * (1 << len(oq)), dtype=torch.float64, device="cuda")
+    P.tn_contract_stem(plan, ids[0], ids[0] + 1, out, stream=stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for sid in ids:
+        P.tn_contract_stem(plan, sid, sid + 1, out, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / len(ids)
+    gold, _ = stored_slices(name)
+    err = None
+    if gold:
+        errs = []
+        for sid, ref in gold.items():
+            P.tn_contract_stem(plan, sid, sid + 1, out, stream=stream)
+            torch.cuda.synchronize()
+            got = out.cpu().numpy().view(np.complex128)
+            errs.append(float(np.linalg.norm(got - ref) / np.linalg.norm(ref)))
+        err = max(errs)
+    del plan
+    torch.cuda.empty_cache()
+    return {"workload": name, "log2_tc_total": info["log2_tc"], "cw": info["cw"],
+            "n_sliced": info["n_sliced"], "slices_timed": len(ids), "ms_per_slice": ms,
+            "stem_tflops": 8 * info["stem_tc_per_slice"] / (ms / 1e3) / 1e12,
+            "batch_days_one_gpu": ms * 2.0 ** info["n_sliced"] / 1e3 / 86400,
+            "rel_l2_vs_fp64_oracle_stored_slices": err,
+            "context": "paper Table 1, Sycamore-53 m=20 on one V100: 266.80 days at total cost 2^62.5 "
+                       "(another circuit and machine)"}
+
+
 def run_reference(args):
     """The oracle arm: the FP64 CPU oracle on bounded samples of the same
     workload (each step one bounded sample: the heaviest stem steps of slice
@@ -950,8 +1004,10 @@ def main():
     # kernel before each pass that reads its branch matrices from the constant bank
     launches_per_step = (info["n_passes_fused"] + info["n_gemm_steps"] + 2) + 1 + info["n_passes_cbank"]
     gemm_large = None
+    twenty = None
     if rank == 0 and not args.no_sweep:
         gemm_large = gemm_large_run(stream, measured_peaks()[0])
+        twenty = twenty_cycle_run(stream)
     samp = None
     if rank == 0 and not args.no_sampling:
         samp = sampling_run(stream, 2 ** info["n_sliced"] / slices_per_s, len(oq))
@@ -988,6 +1044,7 @@ def main():
             "parity": parity,
             "precision_sweep": sweep,
             "tn_cgemm_large": gemm_large,
+            "twenty_cycle": twenty,
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks,
             "amp_norm_check": float(np.linalg.norm(amps)),

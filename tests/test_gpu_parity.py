@@ -612,3 +612,53 @@ def test_diag53_m14_merged_gemm_steps_per_precision(prec, capsys):
         print(f"\ndiag53_m14 merged, {prec}: rel L2 vs FP64 oracle per slice {errs}")
     tol = {"fp32": TOL, "tf32x3": TOL, "bf16x3": 1e-4, "bf16x1": 0.1}[prec]
     assert max(errs) < tol
+
+
+# The 20-cycle workload with its best plan (total cost 2^62.09: cw 30, 23
+# sliced edges; tests/golden/diag53_m20_scheme.json, exported by
+# make_scheme.py with the options it records): real gates, the bench's launch
+# configuration. Slice 0 against the stored FP64 oracle value; 8 seeded
+# slices timed and the whole 64-amplitude batch extrapolated (Supp. A.4:
+# per-subtask time x number of subtasks).
+def test_diag53_m20_best_plan_slice_and_time(capsys):
+    from bench import workload_inputs
+    from synthetic.circuits import SplitMix64
+    sch = json.load(open(os.path.join(GOLD, "diag53_m20_scheme.json")))
+    c, oq, cb = workload_inputs("diag53_m20")
+    net = P.tn_build_network(c, oq, cb)
+    _, _, q, s = net.info()
+    eid = {(int(a), int(b)): e for e, (a, b) in enumerate(zip(q, s))}
+    plan = P.tn_plan_create(net, order=[tuple(x) for x in sch["order"]],
+                            sliced_edges=[eid[tuple(w)] for w in sch["sliced_wires"]],
+                            cw_limit=30, tile_bits=12, max_pass_steps=8)
+    P.tn_plan_prepare(plan)
+    info = P.tn_plan_info(plan)
+    assert info["cw"] == 30 and info["n_sliced"] == 23
+    assert abs(info["log2_tc"] - sch["log2_tc"]) < 1e-6
+    gold_path = os.path.join(GOLD, "diag53_m20_slices.json")
+    err = None
+    if os.path.exists(gold_path):
+        gold = json.load(open(gold_path))
+        assert gold["sliced_wires"] == sch["sliced_wires"]
+        for sid, v in gold["slices"].items():
+            ref = np.asarray(v["re"]) + 1j * np.asarray(v["im"])
+            err = rel_l2(run(plan, int(sid), int(sid) + 1)[0], ref)
+            assert err < TOL, (sid, err)
+    rng = SplitMix64(CONFIGS["diag53_m20"]["bit_seed"])
+    ids = [rng.next() % (1 << info["n_sliced"]) for _ in range(8)]
+    out = torch.zeros(2 * 64, dtype=torch.float64, device="cuda")
+    P.tn_contract_stem(plan, ids[0], ids[0] + 1, out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for sid in ids:
+        P.tn_contract_stem(plan, sid, sid + 1, out)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / len(ids)
+    days = ms * 2.0 ** info["n_sliced"] / 1e3 / 86400
+    with capsys.disabled():
+        print(f"\ndiag53_m20 plan 2^{info['log2_tc']:.2f} (cw {info['cw']}, {info['n_sliced']} sliced): "
+              f"slice 0 rel L2 vs FP64 oracle {err}; {ms:.1f} ms per slice, "
+              f"{8 * info['stem_tc_per_slice'] / (ms / 1e3) / 1e12:.1f} TFLOP/s, one 64-amplitude batch "
+              f"{days:.2f} days on one GPU")
