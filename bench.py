@@ -368,6 +368,48 @@ def gemm_large_run(stream, peaks, shapes=((16384, 512, 512), (16384, 1024, 1024)
             "rows": out}
 
 
+def hyperedge_run(stream):
+    """Sec. 3 hyperedges for the diagonal part of fSim(pi/2, phi): the
+    16-qubit, 8-cycle workload (64 closed bitstrings) as a multi-hypergraph
+    (greedy scheme, FP64 pairwise steps on the GPU) beside its graph network
+    (stem plan, fused FP32 path): plan cost, width and the time for all 64
+    amplitudes; both checked against the FP64 state vector."""
+    import torch
+    import oracle
+    import paper_2005_06787_gb300 as P
+    name = "grid4x4_m8"
+    cfg = CONFIGS[name]
+    c = config_circuit(name)
+    bits = np.asarray([list(random_bits(16, cfg["bit_seed"] + i)) for i in range(cfg["bitstrings"])],
+                      dtype=np.uint8)
+    psi = oracle.statevector(c)
+    ref = np.asarray([oracle.sv_amplitudes(c, [], list(b), psi=psi)[0] for b in bits])
+    out = {}
+    for kind in ("graph", "hyper"):
+        net = P.tn_build_network(c, [], list(bits[0]), hyper=(kind == "hyper"))
+        plan = P.tn_plan_create(net, cw_limit=30, restarts=8)
+        P.tn_plan_prepare(plan, bits, stream=stream)
+        info = P.tn_plan_info(plan)
+        amps = torch.zeros(2 * len(bits), dtype=torch.float64, device="cuda")
+        nsl = 1 << info["n_sliced"]
+        P.tn_contract_stem(plan, 0, nsl, amps, stream=stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        P.tn_contract_stem(plan, 0, nsl, amps, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        got = amps.cpu().numpy().view(np.complex128)
+        out[kind] = {"log2_tc": info["log2_tc"], "cw": info["cw"], "n_sliced": info["n_sliced"],
+                     "ms_all_amplitudes": e0.elapsed_time(e1),
+                     "path": "FP64 pairwise steps" if kind == "hyper" else "fused FP32 stem",
+                     "rel_l2_vs_statevector": float(np.linalg.norm(got - ref) / np.linalg.norm(ref))}
+        del plan
+    out["workload"] = f"{name}: 64 closed bitstrings"
+    out["tc_ratio_graph_over_hyper"] = 2.0 ** (out["graph"]["log2_tc"] - out["hyper"]["log2_tc"])
+    return out
+
+
 def twenty_cycle_run(stream, n_slices: int = 8):
     """The 20-cycle workload on its best stored plan (total cost 2^62.09, 23
     sliced edges, cw 30; tests/golden/diag53_m20_scheme.json) in the bench's
@@ -1005,9 +1047,11 @@ def main():
     launches_per_step = (info["n_passes_fused"] + info["n_gemm_steps"] + 2) + 1 + info["n_passes_cbank"]
     gemm_large = None
     twenty = None
+    hyper = None
     if rank == 0 and not args.no_sweep:
         gemm_large = gemm_large_run(stream, measured_peaks()[0])
         twenty = twenty_cycle_run(stream)
+        hyper = hyperedge_run(stream)
     samp = None
     if rank == 0 and not args.no_sampling:
         samp = sampling_run(stream, 2 ** info["n_sliced"] / slices_per_s, len(oq))
@@ -1045,6 +1089,7 @@ def main():
             "precision_sweep": sweep,
             "tn_cgemm_large": gemm_large,
             "twenty_cycle": twenty,
+            "hyperedges": hyper,
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks,
             "amp_norm_check": float(np.linalg.norm(amps)),

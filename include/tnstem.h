@@ -161,6 +161,26 @@ typedef struct {
 tn_status tn_build_network(const tn_circuit *c, const int32_t *open_qubits, int32_t n_open,
                            const uint8_t *closed_bits, tn_network **out);
 
+/* Sec. 3 and Supp. A.1 (a network is a multi-hypergraph; hyperedges carry
+ * the diagonal parts of gates): the same circuit as tn_build_network, with
+ * each fSim(pi/2, phi) written as the wire swap times
+ * diag(1, -i, -i, e^{-i phi}) - a rank-2 leaf on the two current wire
+ * indices, which the two wires then exchange. An index is created only by
+ * |0> and single-qubit gates: edge e is index (qubit[e], segment[e]), the one
+ * qubit[e]'s segment[e]-th single-qubit gate created (segment 0: its |0>),
+ * and it may join more than two leaves. Leaves are numbered as for
+ * tn_build_network (a two-qubit gate is one leaf either way). Plans of such a
+ * network (tn_plan_create) take a given order or a greedy one in which each
+ * step keeps the shared edges that other tensors still hold, are not sliced
+ * (sliced_edges must be NULL; TN_ERR_PLAN_INFEASIBLE above opts->cw_limit),
+ * and contract on the GPU as FP64 pairwise steps for the single slice [0, 1)
+ * whatever the precision and mode arguments; tn_plan_steps, tn_plan_profile,
+ * tn_plan_features, tn_contract_stem_noalloc and tn_plan_search answer
+ * TN_ERR_UNSUPPORTED for them. Needs |cos theta| <= 1e-12, else
+ * TN_ERR_UNSUPPORTED. No device work. */
+tn_status tn_build_hypernetwork(const tn_circuit *c, const int32_t *open_qubits, int32_t n_open,
+                                const uint8_t *closed_bits, tn_network **out);
+
 /* Number of leaves and edges; edge e is wire segment (qubit[e], segment[e]).
  * Any output pointer may be NULL; arrays hold n_edges entries. */
 tn_status tn_network_info(const tn_network *net, int32_t *n_leaves, int32_t *n_edges,

@@ -10,7 +10,7 @@ from .binding import (  # noqa: F401
     tn_linear_xeb, tn_permute, tn_plan_create, tn_plan_export, tn_plan_info, tn_plan_prepare,
     tn_plan_steps, tn_plan_profile, tn_version, tn_plan_features, tn_plan_search, Mlp, N_FEATURES, EXPORTED, PREC, MODE,
     tn_set_prefix, tn_destroy_plan, tn_destroy_network, tn_frugal_sample,
-    tn_device_status, tn_fp32_fma_peak,
+    tn_device_status, tn_fp32_fma_peak, tn_build_hypernetwork,
 )
 
 

@@ -32,7 +32,7 @@ EXPORTED = [
     "tn_version", "tn_plan_features", "tn_mlp_create", "tn_mlp_n_params", "tn_mlp_set_params",
     "tn_mlp_get_params", "tn_mlp_loss_grad", "tn_mlp_train", "tn_mlp_predict", "tn_mlp_destroy",
     "tn_plan_search", "tn_set_prefix", "tn_destroy_plan", "tn_destroy_network", "tn_frugal_sample",
-    "tn_device_status", "tn_fp32_fma_peak",
+    "tn_device_status", "tn_fp32_fma_peak", "tn_build_hypernetwork",
 ]
 N_FEATURES = 16
 
@@ -109,6 +109,7 @@ def load():
     L = C.CDLL(LIB_PATH)
     vp, i32, i64, u64 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64
     L.tn_build_network.argtypes = [C.POINTER(tn_circuit), vp, i32, vp, C.POINTER(vp)]
+    L.tn_build_hypernetwork.argtypes = [C.POINTER(tn_circuit), vp, i32, vp, C.POINTER(vp)]
     L.tn_network_info.argtypes = [vp, vp, vp, vp, vp]
     L.tn_plan_create.argtypes = [vp, vp, i32, vp, i32, C.POINTER(tn_plan_opts), C.POINTER(vp)]
     L.tn_plan_prepare.argtypes = [vp, vp, i32, vp]
@@ -209,7 +210,10 @@ class Network:
         return nl.value, ne.value, q, s
 
 
-def tn_build_network(circuit, open_qubits: Sequence[int], closed_bits: Sequence[int]) -> Network:
+def tn_build_network(circuit, open_qubits: Sequence[int], closed_bits: Sequence[int],
+                     hyper: bool = False) -> Network:
+    """The circuit's network; hyper=True: tn_build_hypernetwork (diagonal
+    parts of fSim(pi/2, phi) on hyperedges)."""
     L = load()
     g, offs, pairs = circuit.flat()
     g = np.ascontiguousarray(g.reshape(-1), dtype=np.int8)
@@ -220,9 +224,13 @@ def tn_build_network(circuit, open_qubits: Sequence[int], closed_bits: Sequence[
     oq = np.asarray(list(open_qubits) or [0], dtype=np.int32)
     cb = np.asarray(list(closed_bits) or [0], dtype=np.uint8)
     h = C.c_void_p()
-    _check(L.tn_build_network(C.byref(c), oq.ctypes.data, len(open_qubits), cb.ctypes.data,
-                              C.byref(h)))
+    build = L.tn_build_hypernetwork if hyper else L.tn_build_network
+    _check(build(C.byref(c), oq.ctypes.data, len(open_qubits), cb.ctypes.data, C.byref(h)))
     return Network(h, len(open_qubits), circuit.n_qubits - len(open_qubits), (g, offs, pairs))
+
+
+def tn_build_hypernetwork(circuit, open_qubits: Sequence[int], closed_bits: Sequence[int]) -> Network:
+    return tn_build_network(circuit, open_qubits, closed_bits, hyper=True)
 
 
 def tn_set_prefix(net: Network, closed_bits: Sequence[int]) -> None:

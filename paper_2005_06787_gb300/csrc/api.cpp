@@ -7,6 +7,7 @@
 #include <cstring>
 #include <memory>
 #include <new>
+#include <string>
 
 #include "plan.h"
 
@@ -79,6 +80,26 @@ tn_status tn_build_network(const tn_circuit *c, const int32_t *open_qubits, int3
     });
 }
 
+tn_status tn_build_hypernetwork(const tn_circuit *c, const int32_t *open_qubits, int32_t n_open,
+                                const uint8_t *closed_bits, tn_network **out) {
+    return guard([&] {
+        if (!c || !out) tn::fail(TN_ERR_INVALID_ARG, "null argument");
+        auto *n = new tn_network;
+        try {
+            n->net = tn::build_network(*c, open_qubits, n_open, closed_bits, true);
+        } catch (...) {
+            delete n;
+            throw;
+        }
+        *out = n;
+    });
+}
+
+// Calls that only the stem path offers.
+static void require_stem_plan(const tn::Plan &p) {
+    if (p.hyper) tn::fail(TN_ERR_UNSUPPORTED, "not available for a hypergraph plan (no stem)");
+}
+
 tn_status tn_network_info(const tn_network *net, int32_t *n_leaves, int32_t *n_edges,
                           int32_t *qubit, int32_t *segment) {
     return guard([&] {
@@ -105,6 +126,20 @@ tn_status tn_plan_create(tn_network *net, const int32_t *order, int32_t n_pairs,
         auto p = std::make_unique<tn::Plan>();
         p->net = net->net;
         p->opts = o;
+        if (p->net.hyper) {
+            if (n_sliced > 0) tn::fail(TN_ERR_UNSUPPORTED, "hypergraph plans are not sliced");
+            std::vector<std::pair<int, int>> ord((size_t)std::max(n_pairs, 0));
+            for (int i = 0; order && i < n_pairs; ++i) ord[(size_t)i] = {order[2 * i], order[2 * i + 1]};
+            p->hs = tn::hyper_scheme(p->net, order ? &ord : nullptr, o.restarts, o.seed, o.cw_limit);
+            p->hyper = true;
+            if (p->hs.cw > o.cw_limit)
+                tn::fail(TN_ERR_PLAN_INFEASIBLE, "hypergraph scheme wider than cw_limit (" +
+                                                     std::to_string(p->hs.cw) + ")");
+            auto *h = new tn_plan;
+            h->p = std::move(p);
+            *out = h;
+            return;
+        }
         if (order) {
             std::vector<std::pair<int, int>> ord((size_t)std::max(n_pairs, 0));
             for (int i = 0; i < n_pairs; ++i) ord[(size_t)i] = {order[2 * i], order[2 * i + 1]};
@@ -134,7 +169,10 @@ tn_status tn_plan_prepare(tn_plan *plan, const uint8_t *prefixes, int32_t n_pref
         if (!plan) tn::fail(TN_ERR_INVALID_ARG, "null plan");
         if (n_prefixes < 0 || n_prefixes > 4096) tn::fail(TN_ERR_INVALID_ARG, "bad n_prefixes");
         if (n_prefixes > 0 && !prefixes) tn::fail(TN_ERR_INVALID_ARG, "null prefixes");
-        tn::plan_prepare(*plan->p, prefixes, n_prefixes, (cudaStream_t)cuda_stream);
+        if (plan->p->hyper)
+            tn::hyper_prepare(*plan->p, prefixes, n_prefixes, (cudaStream_t)cuda_stream);
+        else
+            tn::plan_prepare(*plan->p, prefixes, n_prefixes, (cudaStream_t)cuda_stream);
     });
 }
 
@@ -143,6 +181,16 @@ tn_status tn_plan_info(const tn_plan *plan, tn_plan_stats *out) {
         if (!plan || !out) tn::fail(TN_ERR_INVALID_ARG, "null argument");
         const tn::Plan &p = *plan->p;
         std::memset(out, 0, sizeof(*out));
+        if (p.hyper) {
+            out->log2_tc = p.hs.log2_tc;
+            out->stem_tc_per_slice = std::exp2(p.hs.log2_tc);
+            out->cw = p.hs.cw;
+            out->n_open = (int)p.net.open_edges.size();
+            out->n_prefixes = p.n_prefix;
+            out->batch_items = std::max(p.n_prefix, 1);
+            out->device_bytes = p.device_bytes;
+            return;
+        }
         out->log2_tc = p.scheme.log2_tc;
         out->stem_tc_per_slice = p.scheme.stem_tc;
         out->branch_tc = p.scheme.branch_tc;
@@ -173,6 +221,13 @@ tn_status tn_plan_export(const tn_plan *plan, int32_t *order, int32_t *sliced_ed
     return guard([&] {
         if (!plan) tn::fail(TN_ERR_INVALID_ARG, "null plan");
         const tn::Plan &p = *plan->p;
+        if (p.hyper) {
+            for (size_t i = 0; order && i < p.hs.pairs.size(); ++i) {
+                order[2 * i] = p.hs.pairs[i].first;
+                order[2 * i + 1] = p.hs.pairs[i].second;
+            }
+            return;
+        }
         if (order) {
             auto ord = tn::export_order(p.net, p.scheme);
             for (size_t i = 0; i < ord.size(); ++i) {
@@ -190,6 +245,7 @@ tn_status tn_plan_steps(const tn_plan *plan, tn_step_info *out, int32_t max_step
     return guard([&] {
         if (!plan) tn::fail(TN_ERR_INVALID_ARG, "null plan");
         const tn::Plan &p = *plan->p;
+        require_stem_plan(p);
         const int L = (int)p.sp.plain_steps.size();
         int w = 0;
         for (int i = 0; i < L && (out && i < max_steps); ++i) {
@@ -219,6 +275,12 @@ tn_status tn_contract_stem(tn_plan *plan, uint64_t slice_begin, uint64_t slice_e
                            double *amps_out, int32_t accumulate) {
     return guard([&] {
         if (!plan) tn::fail(TN_ERR_INVALID_ARG, "null plan");
+        if (plan->p->hyper) {
+            if ((int)prec < 0 || (int)prec > 3) tn::fail(TN_ERR_INVALID_ARG, "bad precision");
+            tn::hyper_contract(*plan->p, slice_begin, slice_end, (cudaStream_t)cuda_stream, amps_out,
+                               accumulate);
+            return;
+        }
         tn::plan_contract(*plan->p, slice_begin, slice_end, prec, mode, (cudaStream_t)cuda_stream,
                           amps_out, accumulate);
     });
@@ -230,6 +292,7 @@ tn_status tn_plan_profile(tn_plan *plan, uint64_t slice_begin, tn_precision prec
     return guard([&] {
         if (!plan || !n_records || (max_records > 0 && !out))
             tn::fail(TN_ERR_INVALID_ARG, "null argument");
+        require_stem_plan(*plan->p);
         auto recs = tn::plan_profile(*plan->p, slice_begin, prec, mode, (cudaStream_t)cuda_stream);
         int w = 0;
         for (size_t i = 0; i < recs.size() && w < max_records; ++i) out[w++] = recs[i];
@@ -241,6 +304,7 @@ tn_status tn_contract_stem_noalloc(tn_plan *plan, uint64_t slice_begin, uint64_t
                                    void *cuda_stream, double *amps_out, int32_t accumulate) {
     return guard([&] {
         if (!plan) tn::fail(TN_ERR_INVALID_ARG, "null plan");
+        require_stem_plan(*plan->p);
         tn::plan_contract_noalloc(*plan->p, slice_begin, slice_end, (cudaStream_t)cuda_stream,
                                   amps_out, accumulate);
     });
@@ -251,6 +315,7 @@ tn_status tn_plan_features(const tn_plan *plan, tn_precision prec, tn_exec_mode 
     return guard([&] {
         if (!plan || !n_rows) tn::fail(TN_ERR_INVALID_ARG, "null argument");
         const tn::Plan &p = *plan->p;
+        require_stem_plan(p);
         const int nsl = (int)p.scheme.sliced_list.size();
         const int npre = std::max(p.n_prefix, 1);
         const int items = mode == TN_EXEC_FUSED
@@ -324,6 +389,7 @@ tn_status tn_plan_search(tn_network *net, const tn_plan_opts *base, const tn_sea
                          tn_mlp *mlp, tn_precision prec, tn_plan **out, tn_search_report *report) {
     return guard([&] {
         if (!net || !out) tn::fail(TN_ERR_INVALID_ARG, "null argument");
+        if (net->net.hyper) tn::fail(TN_ERR_UNSUPPORTED, "plan search needs a graph network (stem plans)");
         tn_plan_opts o = base ? *base : default_opts();
         if (o.cw_limit <= 0) o.cw_limit = 30;
         tn_search_opts s{};

@@ -21,7 +21,7 @@ void Plan::release() {
     if (graph_stream) cudaStreamDestroy(graph_stream);
     graph_stream = nullptr;
     void *ptrs[] = {d_pool, d_branches, d_plain, d_fused, d_chunks, d_buf[0], d_buf[1],
-                    d_state, d_sum, d_comp, d_out, d_pos_plain, d_pos_fused};
+                    d_state, d_sum, d_comp, d_out, d_pos_plain, d_pos_fused, d_hleaf};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     d_pool = nullptr;
@@ -32,6 +32,7 @@ void Plan::release() {
     d_state = nullptr;
     d_sum = d_comp = d_out = nullptr;
     d_pos_plain = d_pos_fused = nullptr;
+    d_hleaf = nullptr;
     device_bytes = 0;
     prepared = false;
 }
@@ -412,6 +413,122 @@ void plan_contract(Plan &p, uint64_t s0, uint64_t s1, tn_precision prec, tn_exec
     if (is_device_pointer(amps_out)) {
         TN_CUDA(launch_finalize(p.d_sum, p.d_comp, reinterpret_cast<double2 *>(amps_out), nout,
                                 accumulate, st));
+    } else {
+        TN_CUDA(launch_finalize(p.d_sum, p.d_comp, p.d_out, nout, 0, st));
+        std::vector<double> h_out((size_t)nout * 2);
+        TN_CUDA(cudaMemcpyAsync(h_out.data(), p.d_out, sizeof(double2) * (size_t)nout,
+                                cudaMemcpyDeviceToHost, st));
+        TN_CUDA(cudaStreamSynchronize(st));
+        for (int64_t i = 0; i < nout * 2; ++i)
+            amps_out[i] = accumulate ? amps_out[i] + h_out[(size_t)i] : h_out[(size_t)i];
+    }
+}
+
+// ------------------------------------------------------------------------
+// Hypergraph plans: every pairwise step of the scheme runs as one FP64
+// contraction on the GPU (small_contract_kernel with the kept shared edges as
+// batch indices), per prefix; intermediates are stream-ordered allocations
+// freed as soon as they are consumed.
+void hyper_prepare(Plan &p, const uint8_t *prefixes, int n_prefixes, cudaStream_t st) {
+    const Network &net = p.net;
+    const int n_closed = (int)net.closed_qubits.size();
+    if (n_prefixes <= 0) {
+        prefixes = nullptr;
+        n_prefixes = 1;
+    }
+    p.release();
+    TN_CUDA(init_kernels());
+    TN_CUDA(cudaGetDevice(&p.device));
+    p.n_prefix = n_prefixes;
+    const int L = net.n_leaves();
+    p.h_leaf_off.assign((size_t)L, 0);
+    int64_t total = 0;
+    for (int i = 0; i < L; ++i) {
+        p.h_leaf_off[(size_t)i] = total;
+        total += (int64_t)net.leaves[(size_t)i].vals.size();
+    }
+    p.h_leaf_total = total;
+    std::vector<double2> h((size_t)(total * n_prefixes));
+    for (int pp = 0; pp < n_prefixes; ++pp)
+        for (int i = 0; i < L; ++i) {
+            const Leaf &lf = net.leaves[(size_t)i];
+            for (size_t v = 0; v < lf.vals.size(); ++v) {
+                cd x = lf.vals[v];
+                if (lf.kind == LEAF_PROJ) {
+                    const uint8_t b = prefixes ? prefixes[(size_t)pp * n_closed + lf.gate]
+                                               : net.closed_bits[(size_t)lf.gate];
+                    if (b > 1) fail(TN_ERR_INVALID_ARG, "prefix bits must be 0 or 1");
+                    x = (v == (size_t)b) ? 1.0 : 0.0;
+                }
+                h[(size_t)(pp * total + p.h_leaf_off[(size_t)i] + (int64_t)v)] = make_double2(x.real(), x.imag());
+            }
+        }
+    p.d_hleaf = dev_alloc<double2>(p, h.size());
+    TN_CUDA(cudaMemcpy(p.d_hleaf, h.data(), h.size() * sizeof(double2), cudaMemcpyHostToDevice));
+    const int nb = 1 << (int)net.open_edges.size();
+    p.d_sum = dev_alloc<double2>(p, (size_t)n_prefixes * nb);
+    p.d_comp = dev_alloc<double2>(p, (size_t)n_prefixes * nb);
+    p.d_out = dev_alloc<double2>(p, (size_t)n_prefixes * nb);
+    TN_CUDA(cudaMemset(p.d_comp, 0, sizeof(double2) * (size_t)n_prefixes * nb));
+    p.prepared = true;
+}
+
+void hyper_contract(Plan &p, uint64_t s0, uint64_t s1, cudaStream_t st, double *amps_out,
+                    int accumulate) {
+    require_plan_device(p);
+    if (s0 > s1 || s1 > 1) fail(TN_ERR_INVALID_ARG, "a hypergraph plan has one slice: range within [0, 1]");
+    if (!amps_out) fail(TN_ERR_INVALID_ARG, "amps_out is null");
+    const Network &net = p.net;
+    const int L = net.n_leaves();
+    const int nb = 1 << (int)net.open_edges.size();
+    const int64_t nout = (int64_t)p.n_prefix * nb;
+    TN_CUDA(cudaMemsetAsync(p.d_sum, 0, sizeof(double2) * (size_t)nout, st));
+    const HyperScheme &hs = p.hs;
+    const size_t np = hs.pairs.size();
+    auto layout = [&](int ref) -> const std::vector<int> & {
+        return ref < L ? net.leaves[(size_t)ref].edges : hs.node_edges[(size_t)(ref - L)];
+    };
+    // all prefixes in each launch: a tensor that depends on a projector has
+    // one copy per prefix (stride = its size), the others one shared copy
+    if (s1 > s0) {
+        std::vector<double2 *> node(np, nullptr);
+        std::vector<char> per_prefix(np, 0);
+        auto dep = [&](int ref) {
+            return ref < L ? net.leaves[(size_t)ref].kind == LEAF_PROJ && p.n_prefix > 1
+                           : (bool)per_prefix[(size_t)(ref - L)];
+        };
+        auto base = [&](int ref) -> const double2 * {
+            return ref < L ? p.d_hleaf + p.h_leaf_off[(size_t)ref] : node[(size_t)(ref - L)];
+        };
+        auto stride = [&](int ref) -> int64_t {
+            if (!dep(ref)) return 0;
+            return ref < L ? p.h_leaf_total : (int64_t)1 << hs.node_edges[(size_t)(ref - L)].size();
+        };
+        for (size_t k = 0; k < np; ++k) {
+            const int a = hs.pairs[k].first, b = hs.pairs[k].second;
+            const std::vector<int> &lc = hs.node_edges[k];
+            const bool last = k + 1 == np;
+            per_prefix[k] = last || dep(a) || dep(b);
+            const int items = per_prefix[k] ? p.n_prefix : 1;
+            double2 *out = p.d_sum;  // last node: prefix-major, 2^n_open each
+            if (!last) {
+                void *q = nullptr;
+                TN_CUDA(cudaMallocAsync(&q, (sizeof(double2) << lc.size()) * (size_t)items, st));
+                out = static_cast<double2 *>(q);
+            }
+            SmallContract d = make_contract(layout(a), layout(b), lc);
+            TN_CUDA(launch_small_contract_batched(base(a), stride(a), base(b), stride(b), out, nullptr,
+                                                  items > 1 ? (int64_t)1 << lc.size() : 0, items, d, st));
+            node[k] = out;
+            for (int r : {a, b})
+                if (r >= L) {
+                    TN_CUDA(cudaFreeAsync(node[(size_t)(r - L)], st));
+                    node[(size_t)(r - L)] = nullptr;
+                }
+        }
+    }
+    if (is_device_pointer(amps_out)) {
+        TN_CUDA(launch_finalize(p.d_sum, p.d_comp, reinterpret_cast<double2 *>(amps_out), nout, accumulate, st));
     } else {
         TN_CUDA(launch_finalize(p.d_sum, p.d_comp, p.d_out, nout, 0, st));
         std::vector<double> h_out((size_t)nout * 2);

@@ -92,7 +92,9 @@ inline int count_xor(const Bits &a, const Bits &b) {
 }
 
 // ----------------------------------------------------------------- network
-enum LeafKind { LEAF_ZERO = 0, LEAF_1Q = 1, LEAF_2Q = 2, LEAF_PROJ = 3 };
+// LEAF_DIAG: in a hypergraph network, the rank-2 diagonal part of fSim(pi/2,
+// phi) on the two wire indices of a gate (the wires then exchange indices).
+enum LeafKind { LEAF_ZERO = 0, LEAF_1Q = 1, LEAF_2Q = 2, LEAF_PROJ = 3, LEAF_DIAG = 4 };
 
 struct Leaf {
     int kind;
@@ -110,6 +112,7 @@ struct EdgeInfo {
 };
 
 struct Network {
+    bool hyper = false;  // multi-hypergraph (an index may join more than two leaves)
     int n_qubits = 0, n_cycles = 0;
     double theta = 0, phi = 0;
     std::vector<Leaf> leaves;
@@ -122,8 +125,29 @@ struct Network {
     int n_leaves() const { return (int)leaves.size(); }
 };
 
+// hyper = true: the multi-hypergraph form (Supp. A.1; Sec. 3, hyperedges for
+// diagonal gate parts): needs fSim(pi/2, phi), the wire swap times a diagonal
+// gate; each two-qubit gate becomes a LEAF_DIAG on the two wire indices.
 Network build_network(const tn_circuit &c, const int32_t *open_qubits, int n_open,
-                      const uint8_t *closed_bits);
+                      const uint8_t *closed_bits, bool hyper = false);
+
+// Contraction scheme of a hypergraph network: SSA pairs over the leaves and
+// the edges each new node keeps (E*_AB of Supp. A.1: the pair's edges that
+// are open or still held by another tensor); the last node keeps the open
+// edges, the first open qubit at the most significant bit. tc sums 2^|E_AB|,
+// cw maxes |E*_AB|.
+struct HyperScheme {
+    std::vector<std::pair<int, int>> pairs;
+    std::vector<std::vector<int>> node_edges;
+    double log2_tc = 0;
+    int cw = 0;
+};
+// order == nullptr: greedy pairs (smallest 2^|out| - 2^|a| - 2^|b|, ties by
+// the smaller ids), over `restarts` runs (all but the first with noise on the
+// scores, from `seed`): the cheapest scheme within cw_limit, else the
+// narrowest; otherwise the given SSA order, validated.
+HyperScheme hyper_scheme(const Network &net, const std::vector<std::pair<int, int>> *order, int restarts,
+                         uint64_t seed, int cw_limit);
 // Re-value the closed-qubit projectors (Sec. 3 post-selection); the structure,
 // and so any plan made from it, is unchanged.
 void set_prefix(Network &net, const uint8_t *closed_bits);

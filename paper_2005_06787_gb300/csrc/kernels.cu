@@ -605,7 +605,12 @@ cudaError_t launch_pass(const DevPass *d_pass, const DevPass &h_pass, const int 
 // (Cf) when it is a finished branch.
 __global__ void small_contract_kernel(const double2 *__restrict__ A, const double2 *__restrict__ B,
                                       double2 *__restrict__ Cd, float2 *__restrict__ Cf,
-                                      SmallContract d) {
+                                      SmallContract d, int64_t sA, int64_t sB, int64_t sC) {
+    // batch item blockIdx.y: operands at item * stride (stride 0: shared)
+    A += blockIdx.y * sA;
+    if (B) B += blockIdx.y * sB;
+    if (Cd) Cd += blockIdx.y * sC;
+    if (Cf) Cf += blockIdx.y * sC;
     const int64_t nout = (int64_t)1 << d.rc;
     const int64_t nsum = (int64_t)1 << d.k;
     for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < nout;
@@ -646,10 +651,18 @@ __global__ void small_contract_kernel(const double2 *__restrict__ A, const doubl
 
 cudaError_t launch_small_contract(const double2 *A, const double2 *B, double2 *Cd, float2 *Cf,
                                   const SmallContract &d, cudaStream_t st) {
+    return launch_small_contract_batched(A, 0, B, 0, Cd, Cf, 0, 1, d, st);
+}
+
+cudaError_t launch_small_contract_batched(const double2 *A, int64_t sA, const double2 *B, int64_t sB,
+                                          double2 *Cd, float2 *Cf, int64_t sC, int items,
+                                          const SmallContract &d, cudaStream_t st) {
+    if (items < 1 || items > 65535) return cudaErrorInvalidValue;
     const int64_t nout = (int64_t)1 << d.rc;
     const int threads = 256;
     const int64_t blocks = std::min<int64_t>((nout + threads - 1) / threads, 4096);
-    small_contract_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), threads, 0, st>>>(A, B, Cd, Cf, d);
+    dim3 grid((unsigned)std::max<int64_t>(blocks, 1), (unsigned)items, 1);
+    small_contract_kernel<<<grid, threads, 0, st>>>(A, B, Cd, Cf, d, sA, sB, sC);
     return cudaGetLastError();
 }
 

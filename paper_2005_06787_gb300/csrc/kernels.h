@@ -75,6 +75,11 @@ cudaError_t launch_pass(const DevPass *d_pass, const DevPass &h_pass, const int 
 // rounds to FP32 into Cf when Cf is given.
 cudaError_t launch_small_contract(const double2 *A, const double2 *B, double2 *Cd, float2 *Cf,
                                   const SmallContract &d, cudaStream_t st);
+// The same over `items` batch items: item i reads A + i sA, B + i sB and
+// writes Cd / Cf + i sC (stride 0: one copy shared by every item).
+cudaError_t launch_small_contract_batched(const double2 *A, int64_t sA, const double2 *B, int64_t sB,
+                                          double2 *Cd, float2 *Cf, int64_t sC, int items,
+                                          const SmallContract &d, cudaStream_t st);
 
 // Stem GEMM step over batch items: C_item[m][nu] = sum_kappa A_item[m][kappa] *
 // Branch_item[kappa][nu]; A item stride 2^r_in, C item stride 2^r_out.

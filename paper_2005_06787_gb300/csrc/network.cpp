@@ -42,7 +42,7 @@ void fsim_matrix(double theta, double phi, cd f[16]) {
 }
 
 Network build_network(const tn_circuit &c, const int32_t *open_qubits, int n_open,
-                      const uint8_t *closed_bits) {
+                      const uint8_t *closed_bits, bool hyper) {
     if (c.n_qubits <= 0 || c.n_qubits > 4096 || c.n_cycles < 0 || c.n_cycles > 4096)
         fail(TN_ERR_INVALID_ARG, "n_qubits / n_cycles out of range");
     if (!c.gates_1q || !c.pair_offsets || (c.pair_offsets[c.n_cycles] > 0 && !c.pairs))
@@ -51,7 +51,10 @@ Network build_network(const tn_circuit &c, const int32_t *open_qubits, int n_ope
         fail(TN_ERR_INVALID_ARG, "bad open-qubit list");
     if (n_open < c.n_qubits && !closed_bits) fail(TN_ERR_INVALID_ARG, "closed_bits is null");
     const int n = c.n_qubits, m = c.n_cycles;
+    if (hyper && std::abs(std::cos(c.theta)) > 1e-12)
+        fail(TN_ERR_UNSUPPORTED, "a hyperedge network needs fSim(pi/2, phi): a wire swap times a diagonal gate");
     Network net;
+    net.hyper = hyper;
     net.n_qubits = n;
     net.n_cycles = m;
     net.theta = c.theta;
@@ -79,8 +82,9 @@ Network build_network(const tn_circuit &c, const int32_t *open_qubits, int n_ope
     };
     auto attach = [&](int e, int leaf) {
         EdgeInfo &E = net.edges[e];
-        if (E.n_ends >= 2) fail(TN_ERR_INVALID_ARG, "internal: edge with three ends");
-        E.ends[E.n_ends++] = leaf;
+        if (E.n_ends >= 2 && !hyper) fail(TN_ERR_INVALID_ARG, "internal: edge with three ends");
+        if (E.n_ends < 2) E.ends[E.n_ends] = leaf;
+        ++E.n_ends;  // a hyperedge may join more than two leaves
     };
     auto add_leaf = [&](Leaf L) {
         int id = (int)net.leaves.size();
@@ -123,6 +127,18 @@ Network build_network(const tn_circuit &c, const int32_t *open_qubits, int n_ope
             used.insert(qa);
             used.insert(qb);
             int ia = cur[qa], ib = cur[qb];
+            if (hyper) {
+                // fSim(pi/2, phi) |x_a x_b> = d(x_a, x_b) |x_b x_a>: the rank-2
+                // diagonal d on the two wire indices, then the wires exchange
+                // them. value[x_a + 2 x_b] = F[(x_b x_a)][(x_a x_b)].
+                Leaf L{LEAF_DIAG, qa, qb, 0, {ia, ib}, std::vector<cd>(4)};
+                for (int xa = 0; xa < 2; ++xa)
+                    for (int xb = 0; xb < 2; ++xb) L.vals[xa + 2 * xb] = f[(xb * 2 + xa) * 4 + (xa * 2 + xb)];
+                add_leaf(L);
+                cur[qa] = ib;
+                cur[qb] = ia;
+                continue;
+            }
             int oa = new_edge(qa, ++seg[qa]);
             int ob = new_edge(qb, ++seg[qb]);
             // bits (ia, ib, oa, ob): value[ia + 2 ib + 4 oa + 8 ob] = F[(oa ob)][(ia ib)]
@@ -147,7 +163,8 @@ Network build_network(const tn_circuit &c, const int32_t *open_qubits, int n_ope
         net.open_edges.push_back(cur[q]);
     }
     for (auto &e : net.edges)
-        if (!e.open && e.n_ends != 2) fail(TN_ERR_INVALID_ARG, "internal: dangling edge");
+        if (!e.open && (hyper ? e.n_ends < 2 : e.n_ends != 2))
+            fail(TN_ERR_INVALID_ARG, "internal: dangling edge");
     return net;
 }
 

@@ -80,6 +80,13 @@ struct Plan {
     std::map<int, cudaGraphExec_t> graphs;  // per precision
     cudaStream_t graph_stream = nullptr;
 
+    // hypergraph networks: a sequence of FP64 pairwise contractions
+    bool hyper = false;
+    HyperScheme hs;
+    double2 *d_hleaf = nullptr;   // leaf values per prefix (FP64)
+    int64_t h_leaf_total = 0;     // entries per prefix copy
+    std::vector<int64_t> h_leaf_off;
+
     ~Plan();
     void release();
 };
@@ -94,6 +101,11 @@ void plan_contract_noalloc(Plan &p, uint64_t s0, uint64_t s1, cudaStream_t st, d
                            int accumulate);
 void plan_contract(Plan &p, uint64_t s0, uint64_t s1, tn_precision prec, tn_exec_mode mode,
                    cudaStream_t st, double *amps_out, int accumulate);
+// Hypergraph plans (hyper.cpp, executor.cu): upload the leaves of each prefix;
+// contract slice range [0, 1) (no slicing) as FP64 pairwise steps on the GPU.
+void hyper_prepare(Plan &p, const uint8_t *prefixes, int n_prefixes, cudaStream_t st);
+void hyper_contract(Plan &p, uint64_t s0, uint64_t s1, cudaStream_t st, double *amps_out,
+                    int accumulate);
 
 #define TN_CUDA(call)                                                                      \
     do {                                                                                   \

@@ -662,3 +662,29 @@ def test_diag53_m20_best_plan_slice_and_time(capsys):
               f"slice 0 rel L2 vs FP64 oracle {err}; {ms:.1f} ms per slice, "
               f"{8 * info['stem_tc_per_slice'] / (ms / 1e3) / 1e12:.1f} TFLOP/s, one 64-amplitude batch "
               f"{days:.2f} days on one GPU")
+
+
+# ------------------------------------------- hypergraph networks (Sec. 3)
+# The circuit as a multi-hypergraph (diagonal part of fSim(pi/2, phi) on two
+# hyperedges): greedy scheme, FP64 pairwise steps on the GPU, amplitudes of
+# every prepared prefix against the FP64 state vector.
+@pytest.mark.parametrize("rows,cols,m,seed,n_open,n_pre", [(4, 4, 8, 1, 0, 64), (3, 4, 8, 71, 4, 3),
+                                                          (4, 5, 12, 3, 6, 2)])
+def test_hypernetwork_plan_matches_statevector(rows, cols, m, seed, n_open, n_pre):
+    c = random_circuit(grid_layout(rows, cols), m, seed)
+    oq = list(range(n_open))
+    nc = c.n_qubits - n_open
+    pres = np.asarray([list(random_bits(nc, 300 + i)) for i in range(n_pre)], dtype=np.uint8)
+    hnet = P.tn_build_hypernetwork(c, oq, list(pres[0]))
+    plan = P.tn_plan_create(hnet, cw_limit=30, restarts=8)
+    P.tn_plan_prepare(plan, pres)
+    got = run(plan, 0, 1)
+    psi = oracle.statevector(c)
+    ref = np.stack([oracle.sv_amplitudes(c, oq, list(pr), psi=psi) for pr in pres])
+    assert rel_l2(got, ref) < 1e-11, rel_l2(got, ref)
+    # ranges add: empty range then the slice again, accumulated into host memory
+    host = np.zeros(2 * got.size)
+    P.tn_contract_stem(plan, 0, 0, host)
+    P.tn_contract_stem(plan, 0, 1, host, accumulate=True)
+    P.tn_contract_stem(plan, 0, 1, host, accumulate=True)
+    assert rel_l2(host.view(np.complex128).reshape(got.shape), 2 * ref) < 1e-11

@@ -246,3 +246,48 @@ def test_infeasible_width_reports_status():
     with pytest.raises(P.TnError) as e:
         P.tn_plan_create(net, cw_limit=6, max_sliced=1)
     assert e.value.status == 4
+
+
+def test_hypernetwork_plan_cost_matches_oracle_and_is_cheaper():
+    # Supp. A.1 cost on the multi-hypergraph (Sec. 3 hyperedges for the
+    # diagonal part of fSim(pi/2, phi)): the library's greedy scheme, exported,
+    # has the tc / cw the oracle computes for the oracle's own hypergraph of
+    # the circuit, and contracting that network in that order gives the state
+    # vector; it costs less than the graph network's stem plan
+    import math
+    from synthetic.circuits import config_circuit
+    c = config_circuit("grid4x4_m8")
+    oq, cb = [0, 1, 2], list(random_bits(13, 5))
+    hnet = P.tn_build_hypernetwork(c, oq, cb)
+    plan = P.tn_plan_create(hnet, cw_limit=30, restarts=8)
+    info = P.tn_plan_info(plan)
+    order, sl = P.tn_plan_export(plan)
+    assert len(sl) == 0
+    onet = oracle.build_hypernetwork(c, oq, cb)
+    nl, ne, q, s = hnet.info()
+    assert nl == len(onet.tensors)
+    labels = sorted({e for el in onet.edges for e in el})
+    assert sorted(zip(q.tolist(), s.tolist())) == labels
+    tc, cw = oracle.tree_cost(onet.edges, onet.open_edges, [tuple(x) for x in order])
+    assert math.isclose(math.log2(tc), info["log2_tc"], rel_tol=0, abs_tol=1e-9) and cw == info["cw"]
+    val = oracle.contract(onet, [tuple(x) for x in order]).reshape(-1)
+    np.testing.assert_allclose(val, oracle.sv_amplitudes(c, oq, cb), atol=1e-13)
+    gplan = P.tn_plan_create(P.tn_build_network(c, oq, cb), cw_limit=30, restarts=2)
+    assert info["log2_tc"] < P.tn_plan_info(gplan)["log2_tc"] - 2
+
+
+def test_hypernetwork_needs_swap_times_diagonal_fsim_and_unsliced_plans():
+    from synthetic.circuits import grid_layout, random_circuit
+    c = random_circuit(grid_layout(2, 3), 3, 4, theta=1.0)
+    with pytest.raises(P.TnError) as e:
+        P.tn_build_hypernetwork(c, [0], list(random_bits(5, 1)))
+    assert e.value.status == 6
+    c = random_circuit(grid_layout(2, 3), 3, 4)
+    hnet = P.tn_build_hypernetwork(c, [0], list(random_bits(5, 1)))
+    with pytest.raises(P.TnError) as e:
+        P.tn_plan_create(hnet, sliced_edges=[3], order=None)
+    assert e.value.status in (1, 6)
+    plan = P.tn_plan_create(hnet, cw_limit=30)
+    with pytest.raises(P.TnError) as e:
+        P.tn_plan_steps(plan)
+    assert e.value.status == 6
