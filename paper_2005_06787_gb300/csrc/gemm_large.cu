@@ -48,6 +48,7 @@ constexpr int LG_THREADS = 512;  // 16 warps
 constexpr int W_PRODUCER = 0, W_MMA = 1, W_ALLOC = 2, W_CONV0 = 4, N_CONV = 8, W_EPI0 = 12;
 constexpr unsigned long long LG_WAIT_NS = 2000000000ull;  // 2 s per wait
 constexpr uint32_t A_BOX_BYTES = 128 * 128;               // 128 rows x 128 B
+constexpr uint32_t EPI_BOX_BYTES = 32 * 128;              // epilogue staging: 32 rows x 32 FP32
 
 // TF32 x3 with A split in place in shared memory (PREC 1).
 template <int PREC>
@@ -61,9 +62,12 @@ struct LgCfg {
     static constexpr uint32_t STAGE_BYTES = 2 * A_BOX_BYTES + B_BYTES * 2;
     static constexpr uint32_t TX_BYTES = A_BOX_BYTES + B_BYTES * 2;
     static constexpr int ACC_COLS = BN * 2;         // TMEM columns per accumulator buffer (main, corrections)
-    static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE_BYTES;
+    static constexpr int EPI_NB = 1;                // epilogue staging boxes per epilogue warp
+    static constexpr size_t RING = (size_t)STAGES * STAGE_BYTES;
+    static constexpr size_t SMEM = 1024 + RING + 4 * EPI_NB * (size_t)EPI_BOX_BYTES;
 };
 static_assert(2 * LgCfg<1>::ACC_COLS <= 512, "two accumulator buffers must fit the SM's 512 TMEM columns");
+static_assert(LgCfg<1>::SMEM + 256 <= 232448, "stages and staging boxes must fit 227 KB of shared memory");
 
 __device__ __forceinline__ uint32_t lg_smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -158,11 +162,74 @@ __device__ __forceinline__ uint32_t lg_sw(int r, int c) {
     return (uint32_t)(r * 128 + (((c ^ r) & 7) << 4));
 }
 
+// TMA store of a shared-memory box to global memory, tracked by the issuing
+// thread's bulk groups (rows and columns past the tensor are not written).
+__device__ __forceinline__ void lg_tma_store2d(const CUtensorMap *map, uint32_t src, int x, int y) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];\n" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(src), "r"(x), "r"(y)
+                 : "memory");
+}
+__device__ __forceinline__ void lg_bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+// at most N of this thread's bulk groups still reading shared memory
+template <int N>
+__device__ __forceinline__ void lg_bulk_wait_read() {
+    asm volatile("cp.async.bulk.wait_group.read %0;\n" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void lg_bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
+
+// Epilogue of one 128 x BN output tile by epilogue warp q (TMEM lanes
+// 32q .. 32q+31 = tile rows 32q .. 32q+31, one per lane): 32 columns at a
+// time, each lane reads its row from TMEM (for x3 the main and correction
+// accumulators, added with round to nearest), writes it into the warp's
+// staging box (32 rows x 128 B, 128-byte swizzle, so the eight lanes of a
+// quarter-warp hit eight bank groups), and lane 0 stores the box with one
+// TMA copy (full 128-byte lines; rows past M are clipped by the copy). A box
+// is rewritten only after the copy that last read it has read it (NB boxes
+// per warp). The caller skips warps whose 32 rows all lie past M.
+template <int BN, bool X3, int NB>
+__device__ __forceinline__ void lg_epilogue_tile(uint32_t tbase, const CUtensorMap *tmC, unsigned char *stage,
+                                                 uint32_t stage_s, int n0, int row0, int lane, uint32_t &nstore) {
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 32, ++nstore) {
+        const uint32_t b = nstore % NB;
+        if (lane == 0 && nstore >= (uint32_t)NB) lg_bulk_wait_read<NB - 1>();
+        __syncwarp();
+        unsigned char *box = stage + b * EPI_BOX_BYTES;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            uint32_t v[16];
+            lg_ld16(tbase + (uint32_t)(c0 + 16 * h), v);
+            if constexpr (X3) {
+                uint32_t w[16];
+                lg_ld16(tbase + (uint32_t)(BN + c0 + 16 * h), w);
+                asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    v[j] = __float_as_uint(__fadd_rn(__uint_as_float(v[j]), __uint_as_float(w[j])));
+            } else {
+                asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                *reinterpret_cast<uint4 *>(box + lg_sw(lane, 4 * h + c)) =
+                    make_uint4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+        }
+        // generic-proxy writes become visible to the copy engine
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncwarp();
+        if (lane == 0) {
+            lg_tma_store2d(tmC, stage_s + b * EPI_BOX_BYTES, n0 + c0, row0);
+            lg_bulk_commit();
+        }
+    }
+}
+
 template <int PREC>
 __global__ void __launch_bounds__(LG_THREADS, 1)
     tc_cgemm_large_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBh,
-                          const __grid_constant__ CUtensorMap tmBl, float *__restrict__ C, int64_t M,
-                          int K2, int N2, int *err) {
+                          const __grid_constant__ CUtensorMap tmBl, const __grid_constant__ CUtensorMap tmC,
+                          int64_t M, int K2, int N2, int *err) {
     using Cf = LgCfg<PREC>;
     constexpr int BN = Cf::BN, S = Cf::STAGES, KBLK = Cf::KBLK;
     constexpr bool X3 = Cf::X3;
@@ -337,8 +404,9 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
         }
     } else if (warp >= W_EPI0) {
         const int q = warp & 3;  // TMEM lanes 32q .. 32q+31 of this warp
-        const int row = q * 32 + lane;
-        uint32_t tile_i = 0;
+        unsigned char *stage = sm + Cf::RING + (size_t)q * Cf::EPI_NB * EPI_BOX_BYTES;
+        const uint32_t stage_s = lg_smem_u32(stage);
+        uint32_t tile_i = 0, nstore = 0;
         bool ok = true;
         for (int64_t t = st0; t < n_tot; t += st_step, ++tile_i) {
             const uint32_t acc = tile_i & 1, use = tile_i >> 1;
@@ -347,37 +415,17 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;\n");
-            const int64_t m = (int64_t)tile_m0(t) + row;
-            const int n0 = tile_n0(t);
-            float *crow = C + m * (int64_t)N2 + n0;
+            const int row0 = tile_m0(t) + 32 * q;
             const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + acc * (uint32_t)Cf::ACC_COLS;
-#pragma unroll 1
-            for (int c0 = 0; c0 < BN; c0 += 16) {
-                uint32_t v[16];
-                lg_ld16(tbase + (uint32_t)c0, v);
-                if constexpr (X3) {
-                    uint32_t w[16];
-                    lg_ld16(tbase + (uint32_t)(BN + c0), w);
-                    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-#pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        v[j] = __float_as_uint(__fadd_rn(__uint_as_float(v[j]), __uint_as_float(w[j])));
-                } else {
-                    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-                }
-                if (m < M) {
-#pragma unroll
-                    for (int j = 0; j < 16; j += 4)
-                        *reinterpret_cast<float4 *>(crow + c0 + j) =
-                            make_float4(__uint_as_float(v[j]), __uint_as_float(v[j + 1]),
-                                        __uint_as_float(v[j + 2]), __uint_as_float(v[j + 3]));
-                }
-            }
+            if ((int64_t)row0 < M)
+                lg_epilogue_tile<BN, X3, Cf::EPI_NB>(tbase, &tmC, stage, stage_s, tile_n0(t), row0, lane, nstore);
             asm volatile("tcgen05.fence::before_thread_sync;\n");
             __syncwarp();
             if (lane == 0) lg_arrive(lg_smem_u32(&tempty_bar[acc]));
         }
         if (!ok) atomicExch(err, 5);
+        if (lane == 0) lg_bulk_wait_all();  // every output copy has completed
+        __syncwarp();
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n");
     __syncthreads();
@@ -403,17 +451,30 @@ struct LtCfg {
     static constexpr int BN = X3 ? 128 : 256;
     static constexpr int KBLK = 64;                       // real K per stage (128 B of BF16 per row)
     static constexpr uint32_t A_SLOT = 2 * A_BOX_BYTES;   // FP32 rows of one k-block (two boxes)
-    static constexpr int S_A = 2;                         // staging slots
-    static constexpr int S_B = 4;                         // B stages (= TMEM A slots)
+#ifndef LT_SA
+#define LT_SA 2
+#endif
+#ifndef LT_SB
+#define LT_SB 4
+#endif
+    static constexpr int S_A = LT_SA;                     // staging slots
+    static constexpr int S_B = LT_SB;                     // B stages (= TMEM A slots)
     static constexpr uint32_t B_BYTES = (uint32_t)BN * 128;
     static constexpr uint32_t B_STAGE = B_BYTES * (X3 ? 2 : 1);
     static constexpr int ACC_COLS = BN * (X3 ? 2 : 1);
     static constexpr int A_COLS = 32 * (X3 ? 2 : 1);     // TMEM columns of one A slot (hi [+ lo])
-    static constexpr size_t SMEM = 1024 + (size_t)S_A * A_SLOT + (size_t)S_B * B_STAGE;
+#ifndef LT_EPI_NB
+#define LT_EPI_NB 1
+#endif
+    static constexpr int EPI_NB = LT_EPI_NB;              // epilogue staging boxes per epilogue warp
+    static constexpr size_t RING = (size_t)S_A * A_SLOT + (size_t)S_B * B_STAGE;
+    static constexpr size_t SMEM = 1024 + RING + 4 * EPI_NB * (size_t)EPI_BOX_BYTES;
 };
-static_assert(LtCfg<2>::ACC_COLS + 4 * LtCfg<2>::A_COLS <= 512 &&
-                  LtCfg<3>::ACC_COLS + 4 * LtCfg<3>::A_COLS <= 512,
+static_assert(LtCfg<2>::ACC_COLS + LtCfg<2>::S_B * LtCfg<2>::A_COLS <= 512 &&
+                  LtCfg<3>::ACC_COLS + LtCfg<3>::S_B * LtCfg<3>::A_COLS <= 512,
               "accumulator and A slots must fit the SM's 512 TMEM columns");
+static_assert(LtCfg<2>::SMEM + 256 <= 232448 && LtCfg<3>::SMEM + 256 <= 232448,
+              "staging ring and B stages must fit 227 KB of shared memory per block");
 
 __device__ __forceinline__ void lt_st16(uint32_t taddr, const uint32_t (&v)[16]) {
     asm volatile(
@@ -434,8 +495,8 @@ __device__ __forceinline__ void lt_mma(uint32_t d, uint32_t a_tmem, uint64_t b, 
 template <int PREC>
 __global__ void __launch_bounds__(LG_THREADS, 1)
     tc_cgemm_tmem_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBh,
-                         const __grid_constant__ CUtensorMap tmBl, float *__restrict__ C, int64_t M,
-                         int K2, int N2, int *err) {
+                         const __grid_constant__ CUtensorMap tmBl, const __grid_constant__ CUtensorMap tmC,
+                         int64_t M, int K2, int N2, int *err) {
     using Cf = LtCfg<PREC>;
     constexpr int BN = Cf::BN, SA = Cf::S_A, SB = Cf::S_B, KBLK = Cf::KBLK;
     constexpr bool X3 = Cf::X3;
@@ -631,8 +692,9 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
         }
     } else if (warp >= W_EPI0) {
         const int q = warp & 3;
-        const int row = q * 32 + lane;
-        uint32_t tile_i = 0;
+        unsigned char *stage = sm + Cf::RING + (size_t)q * Cf::EPI_NB * EPI_BOX_BYTES;
+        const uint32_t stage_s = lg_smem_u32(stage);
+        uint32_t tile_i = 0, nstore = 0;
         bool ok = true;
         for (int64_t t = blockIdx.x; t < n_tot; t += gridDim.x, ++tile_i) {
             if (!lg_wait(lg_smem_u32(&tfull_bar), tile_i & 1)) {
@@ -640,36 +702,17 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;\n");
-            const int64_t m = (int64_t)tile_m0(t) + row;
-            float *crow = C + m * (int64_t)N2 + tile_n0(t);
+            const int row0 = tile_m0(t) + 32 * q;
             const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16);
-#pragma unroll 1
-            for (int c0 = 0; c0 < BN; c0 += 16) {
-                uint32_t v[16];
-                lg_ld16(tbase + (uint32_t)c0, v);
-                if constexpr (X3) {
-                    uint32_t w[16];
-                    lg_ld16(tbase + (uint32_t)(BN + c0), w);
-                    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-#pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        v[j] = __float_as_uint(__fadd_rn(__uint_as_float(v[j]), __uint_as_float(w[j])));
-                } else {
-                    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-                }
-                if (m < M) {
-#pragma unroll
-                    for (int j = 0; j < 16; j += 4)
-                        *reinterpret_cast<float4 *>(crow + c0 + j) =
-                            make_float4(__uint_as_float(v[j]), __uint_as_float(v[j + 1]),
-                                        __uint_as_float(v[j + 2]), __uint_as_float(v[j + 3]));
-                }
-            }
+            if ((int64_t)row0 < M)
+                lg_epilogue_tile<BN, X3, Cf::EPI_NB>(tbase, &tmC, stage, stage_s, tile_n0(t), row0, lane, nstore);
             asm volatile("tcgen05.fence::before_thread_sync;\n");
             __syncwarp();
             if (lane == 0) lg_arrive(lg_smem_u32(&tempty_bar));
         }
         if (!ok) atomicExch(err, 5);
+        if (lane == 0) lg_bulk_wait_all();  // every output copy has completed
+        __syncwarp();
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n");
     __syncthreads();
@@ -761,19 +804,19 @@ cudaError_t run_large(const float2 *A, const float2 *B, float2 *C, int64_t M, in
     lg_prep_b_kernel<PREC><<<(unsigned)std::min<int64_t>((total + 255) / 256, 4096), 256, 0, st>>>(
         B, K, N, bhi, blo);
     e = cudaGetLastError();
-    CUtensorMap ma, mbh, mbl;
+    CUtensorMap ma, mbh, mbl, mc;  // A, B^T hi / lo, C
     const CUtensorMapDataType bt = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     const uint32_t bbox = 32;  // 128 bytes of K per row
     if (e == cudaSuccess &&
         !(encode_2d(&ma, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, A, (uint64_t)K2, (uint64_t)M, 32, 128) &&
           encode_2d(&mbh, bt, esz, bhi, (uint64_t)K2, (uint64_t)N2, bbox, Cf::BN) &&
-          encode_2d(&mbl, bt, esz, blo, (uint64_t)K2, (uint64_t)N2, bbox, Cf::BN)))
+          encode_2d(&mbl, bt, esz, blo, (uint64_t)K2, (uint64_t)N2, bbox, Cf::BN) &&
+          encode_2d(&mc, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, C, (uint64_t)N2, (uint64_t)M, 32, 32)))
         e = cudaErrorInvalidValue;
     if (e == cudaSuccess) {
         const int64_t tiles = ((M + 127) / 128) * (N2 / Cf::BN);
         const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, num_sms));
-        tc_cgemm_large_kernel<PREC><<<grid, LG_THREADS, Cf::SMEM, st>>>(ma, mbh, mbl, reinterpret_cast<float *>(C),
-                                                                       M, K2, N2, err);
+        tc_cgemm_large_kernel<PREC><<<grid, LG_THREADS, Cf::SMEM, st>>>(ma, mbh, mbl, mc, M, K2, N2, err);
         e = cudaGetLastError();
     }
     cudaError_t f = cudaFreeAsync(ws, st);
@@ -806,19 +849,19 @@ cudaError_t run_tmem(const float2 *A, const float2 *B, float2 *C, int64_t M, int
     lg_prep_b_kernel<PREC><<<(unsigned)std::min<int64_t>((total + 255) / 256, 4096), 256, 0, st>>>(
         B, K, N, bhi, blo);
     e = cudaGetLastError();
-    CUtensorMap ma, mbh, mbl;
+    CUtensorMap ma, mbh, mbl, mc;  // A, B^T hi / lo, C
     const CUtensorMapDataType bt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     const uint32_t bbox = 64;  // 128 bytes of K per row
     if (e == cudaSuccess &&
         !(encode_2d(&ma, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, A, (uint64_t)K2, (uint64_t)M, 32, 128) &&
           encode_2d(&mbh, bt, esz, bhi, (uint64_t)K2, (uint64_t)N2, bbox, Cf::BN) &&
-          encode_2d(&mbl, bt, esz, blo, (uint64_t)K2, (uint64_t)N2, bbox, Cf::BN)))
+          encode_2d(&mbl, bt, esz, blo, (uint64_t)K2, (uint64_t)N2, bbox, Cf::BN) &&
+          encode_2d(&mc, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, C, (uint64_t)N2, (uint64_t)M, 32, 32)))
         e = cudaErrorInvalidValue;
     if (e == cudaSuccess) {
         const int64_t tiles = ((M + 127) / 128) * (N2 / Cf::BN);
         const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, num_sms));
-        tc_cgemm_tmem_kernel<PREC><<<grid, LG_THREADS, Cf::SMEM, st>>>(ma, mbh, mbl, reinterpret_cast<float *>(C),
-                                                                      M, K2, N2, err);
+        tc_cgemm_tmem_kernel<PREC><<<grid, LG_THREADS, Cf::SMEM, st>>>(ma, mbh, mbl, mc, M, K2, N2, err);
         e = cudaGetLastError();
     }
     cudaError_t f = cudaFreeAsync(ws, st);
