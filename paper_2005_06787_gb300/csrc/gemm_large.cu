@@ -21,11 +21,15 @@
 //               the stage back to its producer;
 //   warps 12-15 epilogue: each thread reads its TMEM lane (one row), adds
 //               main + correction with round to nearest and stores the row.
-// tc_cgemm_large_kernel (TF32 x3) splits A in place in the shared-memory
-// stage (3 stages; TMEM double-buffered, so the epilogue of a tile overlaps
-// the next tile's MMAs); tc_cgemm_tmem_kernel (BF16 x3, x1) stores hi / lo
-// into tensor memory and takes A from there (a 4-stage B ring beside a small
-// A staging ring, one accumulator). Every wait is on an mbarrier and bounded
+// tc_cgemm_large_kernel splits A in place in the shared-memory stage, with
+// TMEM double-buffered where two accumulators fit (the epilogue of a tile
+// then overlaps the next tile's MMAs): TF32 x3 on 128-column tiles (3
+// stages), BF16 x1 on 256-column tiles (3 stages), BF16 x3 on 256-column
+// tiles (2 stages, one accumulator) when the output fills the GPU's waves;
+// otherwise BF16 x3 runs on tc_cgemm_tmem_kernel, which stores hi / lo into
+// tensor memory and takes A from there (128-column tiles, a 4-stage B ring
+// beside a small A staging ring, one accumulator). The epilogues store
+// through shared memory with TMA. Every wait is on an mbarrier and bounded
 // in time; a wait that gives up records an error code (read by
 // tn_device_status), and the kernel then waits (bounded) for its own copies
 // and MMAs in flight before freeing TMEM.
@@ -50,24 +54,34 @@ constexpr unsigned long long LG_WAIT_NS = 2000000000ull;  // 2 s per wait
 constexpr uint32_t A_BOX_BYTES = 128 * 128;               // 128 rows x 128 B
 constexpr uint32_t EPI_BOX_BYTES = 32 * 128;              // epilogue staging: 32 rows x 32 FP32
 
-// TF32 x3 with A split in place in shared memory (PREC 1).
+// x3 with A split in place in shared memory: TF32 (PREC 1: a stage holds 32
+// real K; the FP32 box becomes hi, lo goes to a second box; 128-column tiles,
+// two accumulator buffers) or BF16 (PREC 2: a stage holds 64 real K as two
+// FP32 boxes, which become the hi and lo BF16 boxes of 128 B per row;
+// 256-column tiles, so each k-block's 64 KB of B and 32 KB of A feed twice
+// the MMAs of a 128-column tile; one accumulator of main + corrections).
 template <int PREC>
 struct LgCfg {
-    static_assert(PREC == 1, "the shared-memory split kernel serves TF32 x3");
-    static constexpr bool X3 = true;
-    static constexpr int BN = 128;                  // real output columns per tile
-    static constexpr int KBLK = 32;                 // real K per stage (128 B of FP32 per row)
-    static constexpr int STAGES = 3;
+    static_assert(PREC >= 1 && PREC <= 3, "the shared-memory split kernel serves TF32 x3, BF16 x3 and BF16 x1");
+    static constexpr bool X3 = PREC != 3;
+    static constexpr bool BF16 = PREC != 1;
+    static constexpr int BN = BF16 ? 256 : 128;     // real output columns per tile
+    static constexpr int KBLK = BF16 ? 64 : 32;     // real K per stage (128 B per row of the MMA type)
+    static constexpr int STAGES = X3 && BF16 ? 2 : 3;
     static constexpr uint32_t B_BYTES = (uint32_t)BN * 128;
-    static constexpr uint32_t STAGE_BYTES = 2 * A_BOX_BYTES + B_BYTES * 2;
-    static constexpr uint32_t TX_BYTES = A_BOX_BYTES + B_BYTES * 2;
-    static constexpr int ACC_COLS = BN * 2;         // TMEM columns per accumulator buffer (main, corrections)
+    static constexpr uint32_t STAGE_BYTES = 2 * A_BOX_BYTES + B_BYTES * (X3 ? 2 : 1);
+    static constexpr uint32_t TX_BYTES = (BF16 ? 2 : 1) * A_BOX_BYTES + B_BYTES * (X3 ? 2 : 1);
+    static constexpr int ACC_COLS = BN * (X3 ? 2 : 1);  // TMEM columns per accumulator buffer (main [, corrections])
+    static constexpr int NACC = 2 * ACC_COLS <= 512 ? 2 : 1;  // accumulator buffers
     static constexpr int EPI_NB = 1;                // epilogue staging boxes per epilogue warp
     static constexpr size_t RING = (size_t)STAGES * STAGE_BYTES;
     static constexpr size_t SMEM = 1024 + RING + 4 * EPI_NB * (size_t)EPI_BOX_BYTES;
 };
-static_assert(2 * LgCfg<1>::ACC_COLS <= 512, "two accumulator buffers must fit the SM's 512 TMEM columns");
-static_assert(LgCfg<1>::SMEM + 256 <= 232448, "stages and staging boxes must fit 227 KB of shared memory");
+static_assert(LgCfg<1>::NACC * LgCfg<1>::ACC_COLS <= 512 && LgCfg<2>::NACC * LgCfg<2>::ACC_COLS <= 512 &&
+                  LgCfg<3>::NACC * LgCfg<3>::ACC_COLS <= 512,
+              "the accumulator buffers must fit the SM's 512 TMEM columns");
+static_assert(LgCfg<1>::SMEM + 256 <= 232448 && LgCfg<2>::SMEM + 256 <= 232448 && LgCfg<3>::SMEM + 256 <= 232448,
+              "stages and staging boxes must fit 227 KB of shared memory");
 
 __device__ __forceinline__ uint32_t lg_smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -131,12 +145,20 @@ __host__ __device__ constexpr uint32_t lg_idesc(int ab, int n, int m) {
     return (1u << 4) | ((uint32_t)ab << 7) | ((uint32_t)ab << 10) | ((uint32_t)(n >> 3) << 17) |
            ((uint32_t)(m >> 4) << 24);
 }
-// kind::tf32 MMA, both operands in shared memory.
+// MMA with both operands in shared memory: kind::tf32, or kind::f16 with
+// BF16 operands.
+template <bool BF16>
 __device__ __forceinline__ void lg_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+    if constexpr (BF16)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc));
+    else
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 __device__ __forceinline__ void lg_commit(uint32_t bar) {
     asm volatile(
@@ -236,7 +258,8 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
     extern __shared__ __align__(1024) unsigned char lg_raw[];
     unsigned char *sm = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(lg_raw) + 1023) & ~(uintptr_t)1023);
-    __shared__ __align__(8) uint64_t full_bar[S], conv_bar[S], empty_bar[S], tfull_bar[2], tempty_bar[2],
+    constexpr int NACC = Cf::NACC;
+    __shared__ __align__(8) uint64_t full_bar[S], conv_bar[S], empty_bar[S], tfull_bar[NACC], tempty_bar[NACC],
         drain_bar;
     __shared__ uint32_t tmem_base;
 
@@ -256,7 +279,7 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
                          "n"(N_CONV));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(lg_smem_u32(&empty_bar[s])));
         }
-        for (int a = 0; a < 2; ++a) {
+        for (int a = 0; a < NACC; ++a) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(lg_smem_u32(&tfull_bar[a])));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;\n" ::"r"(lg_smem_u32(&tempty_bar[a])));
         }
@@ -292,6 +315,7 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
                 }
                 if (tt >= n_tot) return;
                 lg_prefetch2d(&tmA, kk * KBLK, tile_m0(tt));
+                if constexpr (Cf::BF16) lg_prefetch2d(&tmA, kk * KBLK + 32, tile_m0(tt));
             };
             if (st0 < n_tot)
                 for (int kk = 0; kk < LG_PREFETCH; ++kk) prefetch_a(st0, kk);
@@ -309,8 +333,9 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
                     const uint32_t st = sbase + (uint32_t)s * Cf::STAGE_BYTES;
                     const int k = kb * KBLK;
                     lg_tma2d(st, &tmA, k, m0, fb);
+                    if constexpr (Cf::BF16) lg_tma2d(st + A_BOX_BYTES, &tmA, k + 32, m0, fb);
                     lg_tma2d(st + 2 * A_BOX_BYTES, &tmBh, k, n0, fb);
-                    lg_tma2d(st + 2 * A_BOX_BYTES + Cf::B_BYTES, &tmBl, k, n0, fb);
+                    if constexpr (X3) lg_tma2d(st + 2 * A_BOX_BYTES + Cf::B_BYTES, &tmBl, k, n0, fb);
                 }
             }
             if (!ok) atomicExch(err, 5);
@@ -336,9 +361,42 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
                 }
                 unsigned char *a0 = sm + (size_t)s * Cf::STAGE_BYTES;
                 unsigned char *a1 = a0 + A_BOX_BYTES;
-                // chunks 4h .. 4h+3 of the row: hi in place, lo into the second box
+                if constexpr (Cf::BF16) {
+                    // half h of the row: the 32 FP32 values of box h (k 32h ..
+                    // 32h+31) become chunks 4h .. 4h+3 of the hi row (box 0) and
+                    // of the lo row (box 1); the other lane of the row reads what
+                    // this one writes, so both read before either writes
+                    const unsigned char *src = h ? a1 : a0;
+                    float x[32];
 #pragma unroll
-                for (int c = 4 * h; c < 4 * h + 4; ++c) {
+                    for (int c = 0; c < 8; ++c) {
+                        const float4 v = *reinterpret_cast<const float4 *>(src + lg_sw(r, c));
+                        x[4 * c] = v.x; x[4 * c + 1] = v.y; x[4 * c + 2] = v.z; x[4 * c + 3] = v.w;
+                    }
+                    uint32_t hw[16], lw[16];
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const __nv_bfloat162 hb = __floats2bfloat162_rn(x[2 * i], x[2 * i + 1]);
+                        hw[i] = *reinterpret_cast<const uint32_t *>(&hb);
+                        if constexpr (X3) {
+                            const float2 hf = __bfloat1622float2(hb);
+                            const __nv_bfloat162 lb = __floats2bfloat162_rn(x[2 * i] - hf.x, x[2 * i + 1] - hf.y);
+                            lw[i] = *reinterpret_cast<const uint32_t *>(&lb);
+                        }
+                    }
+                    __syncwarp();
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        *reinterpret_cast<uint4 *>(a0 + lg_sw(r, 4 * h + c)) =
+                            make_uint4(hw[4 * c], hw[4 * c + 1], hw[4 * c + 2], hw[4 * c + 3]);
+                        if constexpr (X3)
+                            *reinterpret_cast<uint4 *>(a1 + lg_sw(r, 4 * h + c)) =
+                                make_uint4(lw[4 * c], lw[4 * c + 1], lw[4 * c + 2], lw[4 * c + 3]);
+                    }
+                } else {
+                    // chunks 4h .. 4h+3 of the row: hi in place, lo into the second box
+#pragma unroll
+                    for (int c = 4 * h; c < 4 * h + 4; ++c) {
                     float4 *p = reinterpret_cast<float4 *>(a0 + lg_sw(r, c));
                     const float4 x = *p;
                     float4 hi, lo;
@@ -348,6 +406,7 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
                     hi.w = lg_round_tf32(x.w); lo.w = lg_round_tf32(x.w - hi.w);
                     *p = hi;
                     *reinterpret_cast<float4 *>(a1 + lg_sw(r, c)) = lo;
+                    }
                 }
                 // generic-proxy writes become visible to the tensor core; one
                 // lane per warp signals once the whole warp is done
@@ -359,11 +418,11 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
         if (!ok) atomicExch(err, 5);
     } else if (warp == W_MMA) {
         if (lane == 0) {
-            constexpr uint32_t idesc = lg_idesc(2, BN, 128);  // TF32 operands
+            constexpr uint32_t idesc = lg_idesc(Cf::BF16 ? 1 : 2, BN, 128);  // BF16 / TF32 operands
             uint32_t it = 0, tile_i = 0;
             bool ok = true;
             for (int64_t t = st0; t < n_tot && ok; t += st_step, ++tile_i) {
-                const uint32_t acc = tile_i & 1, use = tile_i >> 1;
+                const uint32_t acc = tile_i % NACC, use = tile_i / NACC;
                 if (!lg_wait(lg_smem_u32(&tempty_bar[acc]), (use & 1) ^ 1)) {
                     ok = false;
                     break;
@@ -384,11 +443,11 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
                         const uint64_t ahi = lg_desc(st + ko), alo = lg_desc(st + A_BOX_BYTES + ko);
                         const uint64_t bhi = lg_desc(st + 2 * A_BOX_BYTES + ko);
                         const uint32_t accum = (kb | ks) != 0;
-                        lg_mma(d, ahi, bhi, idesc, accum);
+                        lg_mma<Cf::BF16>(d, ahi, bhi, idesc, accum);
                         if constexpr (X3) {
                             const uint64_t blo = lg_desc(st + 2 * A_BOX_BYTES + Cf::B_BYTES + ko);
-                            lg_mma(d + BN, ahi, blo, idesc, accum);
-                            lg_mma(d + BN, alo, bhi, idesc, 1u);
+                            lg_mma<Cf::BF16>(d + BN, ahi, blo, idesc, accum);
+                            lg_mma<Cf::BF16>(d + BN, alo, bhi, idesc, 1u);
                         }
                     }
                     lg_commit(lg_smem_u32(&empty_bar[s]));  // stage free once these MMAs are done
@@ -409,7 +468,7 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
         uint32_t tile_i = 0, nstore = 0;
         bool ok = true;
         for (int64_t t = st0; t < n_tot; t += st_step, ++tile_i) {
-            const uint32_t acc = tile_i & 1, use = tile_i >> 1;
+            const uint32_t acc = tile_i % NACC, use = tile_i / NACC;
             if (!lg_wait(lg_smem_u32(&tfull_bar[acc]), use & 1)) {
                 ok = false;
                 break;
@@ -794,7 +853,7 @@ cudaError_t run_large(const float2 *A, const float2 *B, float2 *C, int64_t M, in
     });
     if (attr_err != cudaSuccess) return attr_err;
     const int K2 = 2 * K, N2 = 2 * N;
-    const size_t esz = 4;  // TF32 in FP32 words
+    const size_t esz = Cf::BF16 ? 2 : 4;  // BF16, or TF32 in FP32 words
     const size_t part = (size_t)N2 * K2 * esz;
     void *ws = nullptr;
     cudaError_t e = cudaMallocAsync(&ws, part * 2, st);
@@ -805,8 +864,8 @@ cudaError_t run_large(const float2 *A, const float2 *B, float2 *C, int64_t M, in
         B, K, N, bhi, blo);
     e = cudaGetLastError();
     CUtensorMap ma, mbh, mbl, mc;  // A, B^T hi / lo, C
-    const CUtensorMapDataType bt = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-    const uint32_t bbox = 32;  // 128 bytes of K per row
+    const CUtensorMapDataType bt = Cf::BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const uint32_t bbox = Cf::BF16 ? 64 : 32;  // 128 bytes of K per row
     if (e == cudaSuccess &&
         !(encode_2d(&ma, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, A, (uint64_t)K2, (uint64_t)M, 32, 128) &&
           encode_2d(&mbh, bt, esz, bhi, (uint64_t)K2, (uint64_t)N2, bbox, Cf::BN) &&
@@ -868,11 +927,32 @@ cudaError_t run_tmem(const float2 *A, const float2 *B, float2 *C, int64_t M, int
     return e != cudaSuccess ? e : f;
 }
 
+// 3xBF16 kernel choice: 256-column tiles with A split in shared memory
+// (measured 7-8 % faster per tile pair than the 128-column tensor-memory
+// kernel at full waves) unless they leave more of the last wave idle, e.g.
+// M = 16384, 2N = 1024: 512 wide tiles are 4 waves of 152, 1024 narrow ones
+// 7 waves.
+bool bf16x3_wide_tiles(int64_t M, int64_t N) {
+    const int64_t N2 = 2 * N;
+    if (N2 % LgCfg<2>::BN) return false;
+    static int num_sms = 0;
+    if (!num_sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || num_sms < 1)
+            num_sms = 1;
+    }
+    const int64_t mt = (M + 127) / 128;
+    const int64_t waves_wide = (mt * (N2 / LgCfg<2>::BN) + num_sms - 1) / num_sms;
+    const int64_t waves_narrow = (mt * (N2 / LtCfg<2>::BN) + num_sms - 1) / num_sms;
+    return (double)waves_wide * 2.0 / 1.075 < (double)waves_narrow;
+}
+
 }  // namespace
 
 bool tc_large_supported(int64_t M, int64_t K, int64_t N, tn_precision prec, const void *A, const void *C) {
     if (prec == TN_PREC_FP32_SIMT) return false;
-    const int64_t bn = prec == TN_PREC_BF16x1 ? LtCfg<3>::BN : LtCfg<2>::BN;
+    const int64_t bn = prec == TN_PREC_BF16x1 ? LgCfg<3>::BN : LtCfg<2>::BN;
     const bool aligned = !((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(C)) & 15);
     return aligned && M >= 128 && M < ((int64_t)1 << 31) && K >= 32 && (2 * K) % 64 == 0 &&
            K <= (1 << 20) && (2 * N) % bn == 0 && N <= (1 << 20);
@@ -881,12 +961,15 @@ bool tc_large_supported(int64_t M, int64_t K, int64_t N, tn_precision prec, cons
 cudaError_t launch_tc_cgemm_large(const float2 *A, const float2 *B, float2 *C, int64_t M, int64_t K,
                                   int64_t N, tn_precision prec, int *err, cudaStream_t st) {
     switch (prec) {
-        // measured per precision: TF32 x3 runs faster with A split in place in
-        // shared memory (0.62 vs 0.59 of its peak at M = 65536, K = N = 512),
-        // the BF16 precisions with A in tensor memory (x3: 0.51 vs 0.49)
+        // measured per precision (M = 65536, K = N = 512): TF32 x3 and BF16 x1
+        // run faster with A split in place in shared memory (0.62 vs 0.59 of
+        // the TF32 peak; 0.42 vs 0.38), BF16 x3 on 256-column tiles in shared
+        // memory (0.59 vs 0.55 on 128-column tiles with A in tensor memory)
         case TN_PREC_TF32x3: return run_large<1>(A, B, C, M, (int)K, (int)N, err, st);
-        case TN_PREC_BF16x3: return run_tmem<2>(A, B, C, M, (int)K, (int)N, err, st);
-        case TN_PREC_BF16x1: return run_tmem<3>(A, B, C, M, (int)K, (int)N, err, st);
+        case TN_PREC_BF16x3:
+            return bf16x3_wide_tiles(M, N) ? run_large<2>(A, B, C, M, (int)K, (int)N, err, st)
+                                           : run_tmem<2>(A, B, C, M, (int)K, (int)N, err, st);
+        case TN_PREC_BF16x1: return run_large<3>(A, B, C, M, (int)K, (int)N, err, st);
         default: return cudaErrorInvalidValue;
     }
 }

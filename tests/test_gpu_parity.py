@@ -127,8 +127,11 @@ def test_cgemm_tensor_core_matches_fp64(prec, M, K, N, batch):
 # item) and the large benchmark shape, whose reference is checked on sampled
 # rows (every row must be written: C starts as NaN).
 @pytest.mark.parametrize("prec", ["tf32x3", "bf16x3", "bf16x1"])
+# (38000, 64, 512) and (65536, 512, 512) fill enough waves of the GPU that
+# 3xBF16 takes its 256-column kernel (the others take the 128-column one).
 @pytest.mark.parametrize("M,K,N,batch", [(128, 32, 128, 1), (1000, 64, 128, 1), (130, 32, 256, 2),
-                                         (4096, 256, 64, 1), (2048, 128, 512, 1), (16384, 512, 512, 1)])
+                                         (4096, 256, 64, 1), (2048, 128, 512, 1), (16384, 512, 512, 1),
+                                         (38000, 64, 512, 1), (65536, 512, 512, 1)])
 def test_cgemm_large_tensor_core_matches_fp64(prec, M, K, N, batch):
     A = random_complex((batch, M, K), 31, np.complex64)
     B = random_complex((batch, K, N), 32, np.complex64)
