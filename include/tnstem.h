@@ -93,7 +93,11 @@ typedef struct {
     int32_t max_pass_steps;   /* steps fused into one pass (0 = auto) */
     int32_t gemm_min_kn;      /* steps with k or n >= this run as GEMM (0 = auto) */
     int32_t merge_group;      /* Supp. A.3 branch merging: merge runs of this many
-                                 consecutive stem branches into one (0/1 = off) */
+                                 consecutive stem branches into one (0/1 = off);
+                                 < 0: choose the merges branch by branch, each
+                                 join kept when the plain FLOP-and-memory model
+                                 predicts the whole plan faster (tn_plan_search
+                                 makes the same choice with the learned model) */
     int32_t merge_rank_cap;   /* largest rank of a merged branch (0 = 10) */
     int32_t anneal_iters;     /* simulated-annealing moves on the stem order per
                                  restart (0 = auto: 600 per branch cluster, at
@@ -315,7 +319,10 @@ tn_status tn_mlp_predict(tn_mlp *m, const float *X, int32_t rows, float *y);
 void tn_mlp_destroy(tn_mlp *m);
 
 typedef struct {
-    int32_t n_seeds;        /* stem-growth seeds (each gives 3 x 5 x 3 variants) */
+    int32_t n_seeds;        /* stem-growth seeds (each gives 3 x 5 x 3 variants, plus
+                               one with branch merges chosen branch by branch by
+                               the primary model from the seed's best unmerged
+                               variant, merge_group -1) */
     double fallback_factor;    /* fall back if the MLP pick's plain-model time exceeds
                                this factor times the plain model's best (0 = 4) */
 } tn_search_opts;

@@ -153,6 +153,8 @@ tn_status tn_plan_create(tn_network *net, const int32_t *order, int32_t n_pairs,
             p->scheme = tn::plan_scheme(p->net, o);
         }
         if (o.merge_group >= 2) tn::merge_branches(p->net, p->scheme, o.merge_group, o.merge_rank_cap);
+        if (o.merge_group < 0)
+            p->scheme = tn::choose_merges(p->net, p->scheme, o, nullptr, TN_PREC_FP32_SIMT, nullptr);
         if (p->scheme.cw > 31) tn::fail(TN_ERR_PLAN_INFEASIBLE, "contraction width above 31");
         tn::BuiltStem bs = tn::build_stem_plan(p->net, p->scheme, o);
         p->sp = std::move(bs.sp);

@@ -140,6 +140,65 @@ double flop_model_ms(const LaunchDesc &d, tn_precision prec) {
     return 1e3 * (std::max(d.bytes / HBM_BPS, d.flops / rate) + LAUNCH_S);
 }
 
+// ------------------------------------------------------------------ merges
+// Predicted time of a whole plan: the model's time per batch of SB slices,
+// times the number of batches (the MLP when given, else the plain model).
+static double predicted_total_ms(const Network &net, const Scheme &s, const tn_plan_opts &o, Mlp *mlp,
+                                 tn_precision prec, bool &ok) {
+    ok = false;
+    if (s.cw > o.cw_limit) return INFINITY;
+    BuiltStem st;
+    try {
+        st = build_stem_plan(net, s, o);
+    } catch (const Error &) {
+        return INFINITY;
+    }
+    const int nsl = (int)s.sliced_list.size();
+    const int SB = choose_batch(st.sp.max_rank, nsl, 1, o.slice_batch);
+    const std::vector<LaunchDesc> ls = launch_list(st.sp, TN_EXEC_FUSED, SB);
+    double ms = 0;
+    if (mlp) {
+        std::vector<float> X(ls.size() * N_FEATURES), y(ls.size());
+        for (size_t i = 0; i < ls.size(); ++i) launch_features(ls[i], prec, &X[i * N_FEATURES]);
+        mlp_predict(*mlp, X.data(), (int)ls.size(), y.data());
+        for (float v : y) ms += std::exp((double)v);
+    } else {
+        for (const LaunchDesc &d : ls) ms += flop_model_ms(d, prec);
+    }
+    ok = true;
+    return ms / SB * std::exp2((double)nsl);
+}
+
+// Supp. A.3 branch merging chosen branch by branch (merge_group < 0): going
+// along the stem, stem branch i + 1 joins the merged branch that holds branch
+// i when the model predicts the whole plan faster by more than 0.1 % (the
+// merged branch is contracted once in pre-computation; the stem absorbs it
+// in one step, fused into a pass when it stays small, else as a GEMM step).
+Scheme choose_merges(const Network &net, const Scheme &base, const tn_plan_opts &o, Mlp *mlp,
+                     tn_precision prec, int *n_joins) {
+    const size_t L = base.stem_order.size();
+    std::vector<char> join(L > 0 ? L - 1 : 0, 0);
+    bool ok = false;
+    Scheme cur = base;
+    double best = predicted_total_ms(net, cur, o, mlp, prec, ok);
+    int joins = 0;
+    for (size_t i = 0; i + 1 < L; ++i) {
+        join[i] = 1;
+        Scheme trial = base;
+        merge_branch_runs(net, trial, join, o.merge_rank_cap);
+        const double t = predicted_total_ms(net, trial, o, mlp, prec, ok);
+        if (ok && t < best * (1.0 - 1e-3)) {
+            best = t;
+            cur = std::move(trial);
+            ++joins;
+        } else {
+            join[i] = 0;
+        }
+    }
+    if (n_joins) *n_joins = joins;
+    return cur;
+}
+
 // ------------------------------------------------------------------ search
 
 struct Candidate {
@@ -219,8 +278,60 @@ SearchResult plan_search(const Network &net, const tn_plan_opts &base, const tn_
             for (size_t j = 0; j < cands[i].launches.size(); ++j) ms += std::exp((double)y[r++]);
             mlp_total[i] = ms / cands[i].slices_per_batch * cands[i].n_slices;
         }
-        mlp_pick = (size_t)(std::min_element(mlp_total.begin(), mlp_total.end()) - mlp_total.begin());
     }
+    // per-branch merge choice (merge_group -1): for every stem-growth seed,
+    // from its unmerged candidate the primary model (the MLP when given, else
+    // the plain model) rates fastest, joins chosen one by one by that model;
+    // each result joins the candidates, scored by both models
+    {
+        const std::vector<double> &prim = mlp ? mlp_total : flop_total;
+        std::vector<size_t> best_of_seed;
+        for (size_t i = 0; i < cands.size(); ++i) {
+            if (cands[i].opts.merge_group != 0) continue;
+            size_t k = 0;
+            while (k < best_of_seed.size() && cands[best_of_seed[k]].opts.seed != cands[i].opts.seed) ++k;
+            if (k == best_of_seed.size())
+                best_of_seed.push_back(i);
+            else if (prim[i] < prim[best_of_seed[k]])
+                best_of_seed[k] = i;
+        }
+        for (size_t b : best_of_seed) {
+            Candidate c;
+            c.opts = cands[b].opts;
+            c.opts.merge_group = -1;
+            int joins = 0;
+            c.scheme = choose_merges(net, cands[b].scheme, c.opts, mlp, prec, &joins);
+            if (joins == 0) continue;  // the same plan as its unmerged candidate
+            try {
+                c.stem = build_stem_plan(net, c.scheme, c.opts);
+            } catch (const Error &) {
+                continue;
+            }
+            const int nsl = (int)c.scheme.sliced_list.size();
+            const int SB = choose_batch(c.stem.sp.max_rank, nsl, 1, base.slice_batch);
+            c.items = SB;
+            c.slices_per_batch = SB;
+            c.n_slices = std::exp2((double)nsl);
+            c.launches = launch_list(c.stem.sp, TN_EXEC_FUSED, SB);
+            double fms = 0;
+            for (auto &d : c.launches) fms += flop_model_ms(d, prec);
+            flop_total.push_back(fms / c.slices_per_batch * c.n_slices);
+            double mms = 0;
+            if (mlp) {
+                std::vector<float> X(c.launches.size() * N_FEATURES), y(c.launches.size());
+                for (size_t j = 0; j < c.launches.size(); ++j)
+                    launch_features(c.launches[j], prec, &X[j * N_FEATURES]);
+                mlp_predict(*mlp, X.data(), (int)c.launches.size(), y.data());
+                for (float v : y) mms += std::exp((double)v);
+            }
+            mlp_total.push_back(mms / c.slices_per_batch * c.n_slices);
+            rows += c.launches.size();
+            cands.push_back(std::move(c));
+        }
+    }
+    flop_pick = (size_t)(std::min_element(flop_total.begin(), flop_total.end()) - flop_total.begin());
+    mlp_pick = flop_pick;
+    if (mlp) mlp_pick = (size_t)(std::min_element(mlp_total.begin(), mlp_total.end()) - mlp_total.begin());
     SearchResult res;
     res.n_candidates = (int)cands.size();
     res.n_launch_rows = (int)rows;

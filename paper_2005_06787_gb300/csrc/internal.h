@@ -195,6 +195,7 @@ Scheme scheme_from_order(const Network &net, const std::vector<std::pair<int, in
                          const std::vector<int> &sliced, const tn_plan_opts &opts);
 void evaluate_scheme(const Network &net, Scheme &s);
 void merge_branches(const Network &net, Scheme &s, int group, int rank_cap);
+int merge_branch_runs(const Network &net, Scheme &s, const std::vector<char> &join, int rank_cap);
 std::vector<std::pair<int, int>> export_order(const Network &net, const Scheme &s);
 
 // ----------------------------------------------------------------- device plan

@@ -45,6 +45,10 @@ struct SearchResult {
     Scheme scheme;
     BuiltStem stem;
 };
+// Branch merges chosen one by one along the stem by the model's predicted
+// time (mlp == nullptr: the plain model); returns the merged scheme.
+Scheme choose_merges(const Network &net, const Scheme &base, const tn_plan_opts &o, Mlp *mlp,
+                     tn_precision prec, int *n_joins);
 SearchResult plan_search(const Network &net, const tn_plan_opts &base, const tn_search_opts &so,
                          Mlp *mlp, tn_precision prec);
 

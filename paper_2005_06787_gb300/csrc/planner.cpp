@@ -828,12 +828,30 @@ Scheme scheme_from_order(const Network &net, const std::vector<std::pair<int, in
     return s;
 }
 
+// Absorb cluster b into the merged branch m (b's pair list after m's, then one
+// pair joining the two roots), unless the merged rank (unsliced) would exceed
+// rank_cap or the two share a sliced edge (that edge would be summed inside
+// the branch instead of being fixed per slice).
+static bool absorb_branch(Cluster &m, const Cluster &b, const Bits &sliced, int rank_cap) {
+    if ((m.out & b.out & sliced).any()) return false;
+    if ((m.out ^ b.out).andnot(sliced).count() > rank_cap) return false;
+    // root refs of m and b within the merged pair list
+    const int base = (int)m.pairs.size();
+    const int ra = m.pairs.empty() ? m.leaves[0] : -(int)m.pairs.size();
+    const int rb = b.pairs.empty() ? b.leaves[0] : -((int)b.pairs.size() + base);
+    for (auto p : b.pairs) {
+        auto fix = [&](int r) { return r >= 0 ? r : -((-r - 1) + base + 1); };
+        m.pairs.push_back({fix(p.first), fix(p.second)});
+    }
+    m.pairs.push_back({ra, rb});
+    m.leaves.insert(m.leaves.end(), b.leaves.begin(), b.leaves.end());
+    m.out ^= b.out;
+    return true;
+}
+
 // Supp. A.3 "Branch merging": merge each run of `group` consecutive stem
-// branches into one branch (the pair list of the first, then of the next,
-// then one pair joining them), so the stem absorbs one larger tensor at once.
-// Runs stop early when the merged rank (unsliced) would exceed rank_cap or
-// two members share a sliced edge (that edge would be summed inside the
-// branch instead of being fixed per slice).
+// branches into one branch, so the stem absorbs one larger tensor at once.
+// Runs stop early where absorb_branch refuses the next member.
 void merge_branches(const Network &net, Scheme &s, int group, int rank_cap) {
     if (group < 2 || s.stem_order.empty()) return;
     if (rank_cap <= 0) rank_cap = 10;
@@ -845,21 +863,8 @@ void merge_branches(const Network &net, Scheme &s, int group, int rank_cap) {
         Cluster m = s.clusters[(size_t)s.stem_order[i]];
         int members = 1;
         size_t j = i + 1;
-        while (j < s.stem_order.size() && members < group) {
-            const Cluster &b = s.clusters[(size_t)s.stem_order[j]];
-            if ((m.out & b.out & s.sliced).any()) break;
-            if ((m.out ^ b.out).andnot(s.sliced).count() > rank_cap) break;
-            // root refs of m and b within the merged pair list
-            const int base = (int)m.pairs.size();
-            const int ra = m.pairs.empty() ? m.leaves[0] : -(int)m.pairs.size();
-            int rb = b.pairs.empty() ? b.leaves[0] : -((int)b.pairs.size() + base);
-            for (auto p : b.pairs) {
-                auto fix = [&](int r) { return r >= 0 ? r : -((-r - 1) + base + 1); };
-                m.pairs.push_back({fix(p.first), fix(p.second)});
-            }
-            m.pairs.push_back({ra, rb});
-            m.leaves.insert(m.leaves.end(), b.leaves.begin(), b.leaves.end());
-            m.out ^= b.out;
+        while (j < s.stem_order.size() && members < group &&
+               absorb_branch(m, s.clusters[(size_t)s.stem_order[j]], s.sliced, rank_cap)) {
             ++members;
             ++j;
         }
@@ -871,6 +876,36 @@ void merge_branches(const Network &net, Scheme &s, int group, int rank_cap) {
     s.seed_cluster = 0;
     s.stem_order = std::move(order);
     evaluate_scheme(net, s);
+}
+
+// Branch merging chosen branch by branch: join[i] != 0 puts stem branch i + 1
+// into the merged branch that holds branch i (where absorb_branch allows it;
+// otherwise branch i + 1 starts a new one). Returns the number of joins made.
+int merge_branch_runs(const Network &net, Scheme &s, const std::vector<char> &join, int rank_cap) {
+    if (s.stem_order.empty()) return 0;
+    if (rank_cap <= 0) rank_cap = 10;
+    std::vector<Cluster> out;
+    out.push_back(s.clusters[(size_t)s.seed_cluster]);
+    std::vector<int> order;
+    int joined = 0;
+    size_t i = 0;
+    while (i < s.stem_order.size()) {
+        Cluster m = s.clusters[(size_t)s.stem_order[i]];
+        size_t j = i + 1;
+        while (j < s.stem_order.size() && j - 1 < join.size() && join[j - 1] &&
+               absorb_branch(m, s.clusters[(size_t)s.stem_order[j]], s.sliced, rank_cap)) {
+            ++joined;
+            ++j;
+        }
+        out.push_back(std::move(m));
+        order.push_back((int)out.size() - 1);
+        i = j;
+    }
+    s.clusters = std::move(out);
+    s.seed_cluster = 0;
+    s.stem_order = std::move(order);
+    evaluate_scheme(net, s);
+    return joined;
 }
 
 // SSA order over the leaves: every cluster's internal pairs, then the stem.

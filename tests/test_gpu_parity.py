@@ -555,6 +555,25 @@ def test_diag53_m12_slices_match_stored_oracle(mode):
         assert rel_l2(got, ref) < TOL, (sid, rel_l2(got, ref))
 
 
+def test_diag53_m12_per_branch_merges_match_stored_oracle(capsys):
+    # merge_group -1: the plain model chooses which consecutive branches to
+    # merge; the stored scheme's slices must come out the same
+    plan, gold = _stored_m12_plan(merge_group=-1)
+    base, _ = _stored_m12_plan()
+    info, info0 = P.tn_plan_info(plan), P.tn_plan_info(base)
+    assert info["n_branches"] < info0["n_branches"]
+    P.tn_plan_prepare(plan)
+    errs = []
+    for sid, v in gold["slices"].items():
+        ref = np.asarray(v["re"]) + 1j * np.asarray(v["im"])
+        got = run(plan, int(sid), int(sid) + 1)[0]
+        errs.append(rel_l2(got, ref))
+    with capsys.disabled():
+        print(f"\ndiag53_m12 per-branch merges ({info0['n_branches']} -> {info['n_branches']} branches, "
+              f"{info['n_gemm_steps']} GEMM steps): rel L2 vs FP64 oracle per slice {errs}")
+    assert max(errs) < TOL
+
+
 @pytest.mark.parametrize("prec", ["fp32", "tf32x3", "bf16x3", "bf16x1"])
 def test_diag53_m12_merged_gemm_steps_per_precision(prec, capsys):
     # branch merging (runs of 3) turns most stem steps into GEMM steps

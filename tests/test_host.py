@@ -79,6 +79,50 @@ def test_planned_scheme_value_equals_statevector(rows, cols, m, cw, n_open):
     assert math.log2(tc) == pytest.approx(info["log2_tc"], abs=1e-9)
 
 
+@pytest.mark.parametrize("rows,cols,m,cw,n_open,joins", [(3, 4, 10, 8, 2, True), (3, 3, 6, 5, 2, False)])
+def test_per_branch_merges_keep_the_value_and_lower_the_predicted_time(rows, cols, m, cw, n_open, joins):
+    # merge_group -1: branch merges chosen one by one along the stem by the
+    # plain FLOP-and-memory model; the merged scheme (merged branches are
+    # subtrees of the exported order) still equals the state vector, and its
+    # tc/cw are the oracle's for that order
+    c = random_circuit(grid_layout(rows, cols), m, rows * 100 + m)
+    oq = list(range(n_open))
+    net, cb = _net(c, oq, 17)
+    plan = P.tn_plan_create(net, cw_limit=cw, restarts=4, merge_group=-1)
+    info = P.tn_plan_info(plan)
+    base = P.tn_plan_info(P.tn_plan_create(net, cw_limit=cw, restarts=4))
+    assert info["cw"] <= cw
+    # the 3 x 4 circuit gets at least one merge, the 3 x 3 one none
+    assert (info["n_branches"] < base["n_branches"]) == joins
+    assert info["log2_tc"] <= base["log2_tc"] + 1e-9
+    order, sl = P.tn_plan_export(plan)
+    edges = _oracle_edges(net)
+    sliced = [edges[e] for e in sl]
+    onet = oracle.build_network(c, oq, cb)
+    tot = oracle.contract_sliced_sum(onet, sliced, [tuple(x) for x in order])
+    np.testing.assert_allclose(tot.reshape(-1), oracle.sv_amplitudes(c, oq, cb), atol=1e-13)
+    tc, ocw = oracle.tree_cost(onet.edges, onet.open_edges, [tuple(x) for x in order], sliced)
+    assert ocw == info["cw"]
+    assert math.log2(tc) == pytest.approx(info["log2_tc"], abs=1e-9)
+
+
+def test_per_branch_merges_on_the_12_cycle_workload():
+    # the plain model joins only branches whose merge it predicts faster:
+    # far fewer than the uniform runs of merge_group 3, never more stem cost
+    name = "diag53_m12"
+    cfg = CONFIGS[name]
+    c = config_circuit(name)
+    oq = c.layout.open_qubits(cfg["n_open"])
+    net, _ = _net(c, oq, cfg["bit_seed"])
+    kw = dict(cw_limit=cfg["cw_limit"], restarts=1, anneal_iters=20000)
+    i0 = P.tn_plan_info(P.tn_plan_create(net, **kw))
+    i1 = P.tn_plan_info(P.tn_plan_create(net, merge_group=-1, **kw))
+    i3 = P.tn_plan_info(P.tn_plan_create(net, merge_group=3, **kw))
+    assert i3["n_branches"] < i1["n_branches"] <= i0["n_branches"]
+    assert i1["log2_tc"] <= i0["log2_tc"] + 1e-9
+    assert i1["n_gemm_steps"] < i3["n_gemm_steps"]
+
+
 def test_given_order_round_trip():
     c = random_circuit(grid_layout(3, 4), 8, 3)
     net, _ = _net(c, [0, 1], 5)
