@@ -249,6 +249,9 @@ def dist_env():
 # FP32 FMA rate from unit counts and clock (152 SMs x 128 FP32 lanes x 2 flops
 # x 2.07 GHz): used only when the library's measured rate is unavailable.
 FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# TF32 tensor peak: the measured BF16 peak times the nominal dense TF32 / BF16
+# ratio of this GPU (1.1 / 2.25 PFLOP/s)
+TF32_PER_BF16 = 1.1 / 2.25
 
 
 # DRAM traffic of the dominant kernel: one earlier ncu capture of
@@ -325,7 +328,7 @@ def gemm_large_run(stream, peaks, shapes=((16384, 512, 512), (16384, 1024, 1024)
     """tn_cgemm on large complex shapes (Supp. A.3: merged branches make stem
     steps dense GEMMs) per precision: the TMA-pipelined tcgen05 kernel for the
     tensor-core precisions, the SIMT kernel for FP32. Executed flops count 3
-    products for the x3 precisions; the peak is the measured BF16 one (x0.5
+    products for the x3 precisions; the peak is the measured BF16 one (x1.1/2.25
     for TF32). Each call includes its B split and workspace; inputs resident,
     CUDA events around 20 back-to-back calls; error on 64 sampled rows against
     an FP64 product of the same FP32 inputs."""
@@ -355,7 +358,7 @@ def gemm_large_run(stream, peaks, shapes=((16384, 512, 512), (16384, 1024, 1024)
             got = C.view(-1, 2 * N).cpu().numpy()[rows].view(np.complex64).astype(np.complex128)
             alg = 8.0 * M * K * N
             mult = 3 if prec in ("tf32x3", "bf16x3") else 1
-            peak = peaks["bf16_tflops"] * (0.5 if prec == "tf32x3" else 1.0)
+            peak = peaks["bf16_tflops"] * (TF32_PER_BF16 if prec == "tf32x3" else 1.0)
             exe = mult * alg / (ms * 1e-3) / 1e12
             out.append({"M": M, "K": K, "N": N, "prec": prec, "ms_per_call": ms,
                         "alg_tflops": alg / (ms * 1e-3) / 1e12, "exec_tflops": exe,
@@ -364,7 +367,8 @@ def gemm_large_run(stream, peaks, shapes=((16384, 512, 512), (16384, 1024, 1024)
         del A, B, C
         torch.cuda.empty_cache()
     P.tn_device_status()
-    return {"peak_bf16_tflops": peaks["bf16_tflops"], "peak_note": "measured BF16 burst; TF32 = 0.5 x",
+    return {"peak_bf16_tflops": peaks["bf16_tflops"],
+            "peak_note": f"measured BF16 burst; TF32 = {TF32_PER_BF16:.4f} x (nominal dense TF32 / BF16 rate)",
             "rows": out}
 
 
@@ -1023,7 +1027,7 @@ def main():
             gtf = sum(r["flops"] for r in g) / (gms / 1e3) / 1e12 if gms else None
             # executed tensor flops: 3 products for x3, 1 for x1 (algorithmic = one product)
             mult = {"fp32": 1, "tf32x3": 3, "bf16x3": 3, "bf16x1": 1}[prec]
-            peak = peaks_all.get("bf16_tflops", 1900.0) * (0.5 if prec == "tf32x3" else 1.0)
+            peak = peaks_all.get("bf16_tflops", 1900.0) * (TF32_PER_BF16 if prec == "tf32x3" else 1.0)
             sweep[prec] = {"slices_per_s": sps, "stem_tflops": sps * mflops / 1e12,
                            "rel_l2_vs_fp64_oracle": err,
                            "gemm_share": gms / sum(r["ms"] for r in recs),
