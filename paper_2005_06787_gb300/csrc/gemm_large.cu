@@ -60,23 +60,31 @@ constexpr uint32_t EPI_BOX_BYTES = 32 * 128;              // epilogue staging: 3
 // FP32 boxes, which become the hi and lo BF16 boxes of 128 B per row;
 // 256-column tiles, so each k-block's 64 KB of B and 32 KB of A feed twice
 // the MMAs of a 128-column tile; one accumulator of main + corrections).
-template <int PREC>
+// BNX > 0 sets the tile width (32 or 64 for narrow outputs, e.g. the stem's
+// own GEMM steps); the ring then holds as many stages as fit (up to 6).
+template <int PREC, int BNX = 0>
 struct LgCfg {
     static_assert(PREC >= 1 && PREC <= 3, "the shared-memory split kernel serves TF32 x3, BF16 x3 and BF16 x1");
     static constexpr bool X3 = PREC != 3;
     static constexpr bool BF16 = PREC != 1;
-    static constexpr int BN = BF16 ? 256 : 128;     // real output columns per tile
+    static constexpr int BN = BNX ? BNX : (BF16 ? 256 : 128);  // real output columns per tile
+    static_assert(BN % 32 == 0 && BN >= 32 && BN <= 256, "tile width: a multiple of 32 up to 256");
     static constexpr int KBLK = BF16 ? 64 : 32;     // real K per stage (128 B per row of the MMA type)
-    static constexpr int STAGES = X3 && BF16 ? 2 : 3;
     static constexpr uint32_t B_BYTES = (uint32_t)BN * 128;
     static constexpr uint32_t STAGE_BYTES = 2 * A_BOX_BYTES + B_BYTES * (X3 ? 2 : 1);
     static constexpr uint32_t TX_BYTES = (BF16 ? 2 : 1) * A_BOX_BYTES + B_BYTES * (X3 ? 2 : 1);
     static constexpr int ACC_COLS = BN * (X3 ? 2 : 1);  // TMEM columns per accumulator buffer (main [, corrections])
     static constexpr int NACC = 2 * ACC_COLS <= 512 ? 2 : 1;  // accumulator buffers
     static constexpr int EPI_NB = 1;                // epilogue staging boxes per epilogue warp
+    static constexpr size_t FIXED = 1024 + 4 * EPI_NB * (size_t)EPI_BOX_BYTES + 256;
+    static constexpr int STAGES_FIT = (int)((232448 - FIXED) / STAGE_BYTES);
+    static constexpr int STAGES = STAGES_FIT > 6 ? 6 : STAGES_FIT;
+    static_assert(STAGES >= 2, "at least two stages");
     static constexpr size_t RING = (size_t)STAGES * STAGE_BYTES;
     static constexpr size_t SMEM = 1024 + RING + 4 * EPI_NB * (size_t)EPI_BOX_BYTES;
 };
+static_assert(LgCfg<1>::STAGES == 3 && LgCfg<2>::STAGES == 2 && LgCfg<3>::STAGES == 3,
+              "ring depths of the wide tiles as measured");
 static_assert(LgCfg<1>::NACC * LgCfg<1>::ACC_COLS <= 512 && LgCfg<2>::NACC * LgCfg<2>::ACC_COLS <= 512 &&
                   LgCfg<3>::NACC * LgCfg<3>::ACC_COLS <= 512,
               "the accumulator buffers must fit the SM's 512 TMEM columns");
@@ -247,12 +255,12 @@ __device__ __forceinline__ void lg_epilogue_tile(uint32_t tbase, const CUtensorM
     }
 }
 
-template <int PREC>
+template <int PREC, int BNX>
 __global__ void __launch_bounds__(LG_THREADS, 1)
     tc_cgemm_large_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBh,
                           const __grid_constant__ CUtensorMap tmBl, const __grid_constant__ CUtensorMap tmC,
                           int64_t M, int K2, int N2, int *err) {
-    using Cf = LgCfg<PREC>;
+    using Cf = LgCfg<PREC, BNX>;
     constexpr int BN = Cf::BN, S = Cf::STAGES, KBLK = Cf::KBLK;
     constexpr bool X3 = Cf::X3;
     extern __shared__ __align__(1024) unsigned char lg_raw[];
@@ -267,7 +275,8 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
     const int n_tiles = N2 / BN;
     const int64_t n_tot = ((M + 127) / 128) * n_tiles;
     const int64_t st0 = blockIdx.x, st_step = gridDim.x;
-    const int kblocks = K2 / KBLK;
+    // k-blocks along 2K; a last partial one reads zeros past 2K (TMA fill)
+    const int kblocks = (K2 + KBLK - 1) / KBLK;
     // first row / column of tile t (rows past M are read as zero and not stored)
     auto tile_m0 = [&](int64_t t) { return (int)((t / n_tiles) * 128); };
     auto tile_n0 = [&](int64_t t) { return (int)((t % n_tiles) * BN); };
@@ -315,7 +324,7 @@ __global__ void __launch_bounds__(LG_THREADS, 1)
                 }
                 if (tt >= n_tot) return;
                 lg_prefetch2d(&tmA, kk * KBLK, tile_m0(tt));
-                if constexpr (Cf::BF16) lg_prefetch2d(&tmA, kk * KBLK + 32, tile_m0(tt));
+                if (Cf::BF16 && kk * KBLK + 32 < K2) lg_prefetch2d(&tmA, kk * KBLK + 32, tile_m0(tt));
             };
             if (st0 < n_tot)
                 for (int kk = 0; kk < LG_PREFETCH; ++kk) prefetch_a(st0, kk);
@@ -807,6 +816,46 @@ __global__ void lg_prep_b_kernel(const float2 *__restrict__ B, int K, int N, voi
     }
 }
 
+// The same split for a stem GEMM step with one batch item: B is the branch's
+// matrix for the launch's prefix and slice (read from the device-side batch
+// state, so a captured graph replays it for every slice).
+template <int PREC>
+__global__ void lg_prep_b_stem_kernel(const DevBranch *__restrict__ br, const float2 *__restrict__ pool,
+                                      BatchArgs ba, int K, int N, void *hi_out, void *lo_out) {
+    int64_t o = br->base + (int64_t)ba.p0 * br->prefix_stride;
+    const int64_t sl = ba.state->slice_base;
+    for (int i = 0; i < br->n_sl; ++i)
+        if ((sl >> br->sl_bit[i]) & 1) o += (int64_t)1 << br->sl_pos[i];
+    const float2 *B = pool + o;
+    const int64_t K2 = 2 * (int64_t)K, total = 2 * (int64_t)N * K2;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = i / K2, kk = i % K2;
+        const int nu = (int)(j >> 1), d = (int)(j & 1), kap = (int)(kk >> 1), c = (int)(kk & 1);
+        const float2 b = B[(int64_t)kap * N + nu];
+        const float v = (c == d) ? b.x : (c == 1 ? -b.y : b.y);
+        if constexpr (PREC == 1) {
+            const float h = lg_round_tf32(v);
+            reinterpret_cast<float *>(hi_out)[i] = h;
+            reinterpret_cast<float *>(lo_out)[i] = lg_round_tf32(v - h);
+        } else {
+            const __nv_bfloat16 h = __float2bfloat16_rn(v);
+            reinterpret_cast<__nv_bfloat16 *>(hi_out)[i] = h;
+            if constexpr (PREC == 2)
+                reinterpret_cast<__nv_bfloat16 *>(lo_out)[i] = __float2bfloat16_rn(v - __bfloat162float(h));
+        }
+    }
+}
+
+// Where B comes from: a complex K x N matrix, or (stem steps) a branch of
+// the pool selected for the launch's batch item on the device.
+struct LgBSource {
+    const float2 *B = nullptr;
+    const DevBranch *br = nullptr;
+    const float2 *pool = nullptr;
+    BatchArgs ba{};
+};
+
 // The driver's tensor-map encoder, looked up through the runtime so that the
 // library does not link against the driver library itself (it then still
 // loads on hosts without a GPU driver, where only the planner is used).
@@ -837,16 +886,16 @@ bool encode_2d(CUtensorMap *map, CUtensorMapDataType dt, size_t esz, const void 
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int PREC>
-cudaError_t run_large(const float2 *A, const float2 *B, float2 *C, int64_t M, int K, int N, int *err,
+template <int PREC, int BNX = 0>
+cudaError_t run_large(const float2 *A, const LgBSource &bs, float2 *C, int64_t M, int K, int N, int *err,
                       cudaStream_t st) {
-    using Cf = LgCfg<PREC>;
+    using Cf = LgCfg<PREC, BNX>;
     static std::once_flag attr_once;
     static cudaError_t attr_err = cudaSuccess;
     static int num_sms = 0;
     std::call_once(attr_once, [] {
-        attr_err = cudaFuncSetAttribute(tc_cgemm_large_kernel<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)Cf::SMEM);
+        attr_err = cudaFuncSetAttribute(tc_cgemm_large_kernel<PREC, BNX>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cf::SMEM);
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
@@ -860,8 +909,11 @@ cudaError_t run_large(const float2 *A, const float2 *B, float2 *C, int64_t M, in
     if (e != cudaSuccess) return e;
     unsigned char *bhi = static_cast<unsigned char *>(ws), *blo = bhi + part;
     const int64_t total = (int64_t)N2 * K2;
-    lg_prep_b_kernel<PREC><<<(unsigned)std::min<int64_t>((total + 255) / 256, 4096), 256, 0, st>>>(
-        B, K, N, bhi, blo);
+    const unsigned pgrid = (unsigned)std::min<int64_t>((total + 255) / 256, 4096);
+    if (bs.br)
+        lg_prep_b_stem_kernel<PREC><<<pgrid, 256, 0, st>>>(bs.br, bs.pool, bs.ba, K, N, bhi, blo);
+    else
+        lg_prep_b_kernel<PREC><<<pgrid, 256, 0, st>>>(bs.B, K, N, bhi, blo);
     e = cudaGetLastError();
     CUtensorMap ma, mbh, mbl, mc;  // A, B^T hi / lo, C
     const CUtensorMapDataType bt = Cf::BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
@@ -875,7 +927,7 @@ cudaError_t run_large(const float2 *A, const float2 *B, float2 *C, int64_t M, in
     if (e == cudaSuccess) {
         const int64_t tiles = ((M + 127) / 128) * (N2 / Cf::BN);
         const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, num_sms));
-        tc_cgemm_large_kernel<PREC><<<grid, LG_THREADS, Cf::SMEM, st>>>(ma, mbh, mbl, mc, M, K2, N2, err);
+        tc_cgemm_large_kernel<PREC, BNX><<<grid, LG_THREADS, Cf::SMEM, st>>>(ma, mbh, mbl, mc, M, K2, N2, err);
         e = cudaGetLastError();
     }
     cudaError_t f = cudaFreeAsync(ws, st);
@@ -948,30 +1000,91 @@ bool bf16x3_wide_tiles(int64_t M, int64_t N) {
     return (double)waves_wide * 2.0 / 1.075 < (double)waves_narrow;
 }
 
+// Kernel for a shape: 0 none; 1 the precision's default tile width; 2 the
+// 3xBF16 tensor-memory kernel (128 columns); 3 / 4 the shared-memory split
+// kernel on 64- / 32-column tiles (narrow outputs such as the stem's own
+// GEMM steps). plain_b: B is a plain matrix (the tensor-memory kernel reads
+// no branch pool).
+int large_variant(tn_precision prec, int64_t M, int64_t K2, int64_t N2, bool plain_b) {
+    if (K2 % 32 || N2 % 32) return 0;
+    const bool dflt = N2 % LgCfg<(int)TN_PREC_TF32x3>::BN == 0;
+    switch (prec) {
+        case TN_PREC_TF32x3:
+            if (dflt) return 1;
+            break;
+        case TN_PREC_BF16x3:
+            if (N2 % LgCfg<2>::BN == 0 && bf16x3_wide_tiles(M, N2 / 2)) return 1;
+            if (plain_b && N2 % LtCfg<2>::BN == 0 && K2 % LtCfg<2>::KBLK == 0) return 2;
+            break;
+        case TN_PREC_BF16x1:
+            if (N2 % LgCfg<3>::BN == 0) return 1;
+            break;
+        default: return 0;
+    }
+    return N2 % 64 == 0 ? 3 : 4;
+}
+
+template <int PREC>
+cudaError_t run_variant(int v, const float2 *A, const LgBSource &bs, float2 *C, int64_t M, int K, int N, int *err,
+                        cudaStream_t st) {
+    switch (v) {
+        case 1: return run_large<PREC>(A, bs, C, M, K, N, err, st);
+        case 2:
+            if constexpr (PREC == 2) return run_tmem<PREC>(A, bs.B, C, M, K, N, err, st);
+            return cudaErrorInvalidValue;
+        case 3: return run_large<PREC, 64>(A, bs, C, M, K, N, err, st);
+        case 4: return run_large<PREC, 32>(A, bs, C, M, K, N, err, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t run_any(tn_precision prec, const float2 *A, const LgBSource &bs, float2 *C, int64_t M, int64_t K,
+                    int64_t N, int *err, cudaStream_t st) {
+    const int v = large_variant(prec, M, 2 * K, 2 * N, bs.br == nullptr);
+    // measured per precision (M = 65536, K = N = 512): TF32 x3 and BF16 x1 run
+    // faster with A split in place in shared memory (0.62 vs 0.59 of the TF32
+    // peak; 0.42 vs 0.38), BF16 x3 on 256-column tiles in shared memory (0.59
+    // vs 0.55 on 128-column tiles with A in tensor memory)
+    switch (prec) {
+        case TN_PREC_TF32x3: return run_variant<1>(v, A, bs, C, M, (int)K, (int)N, err, st);
+        case TN_PREC_BF16x3: return run_variant<2>(v, A, bs, C, M, (int)K, (int)N, err, st);
+        case TN_PREC_BF16x1: return run_variant<3>(v, A, bs, C, M, (int)K, (int)N, err, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 }  // namespace
 
 bool tc_large_supported(int64_t M, int64_t K, int64_t N, tn_precision prec, const void *A, const void *C) {
     if (prec == TN_PREC_FP32_SIMT) return false;
-    const int64_t bn = prec == TN_PREC_BF16x1 ? LgCfg<3>::BN : LtCfg<2>::BN;
     const bool aligned = !((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(C)) & 15);
-    return aligned && M >= 128 && M < ((int64_t)1 << 31) && K >= 32 && (2 * K) % 64 == 0 &&
-           K <= (1 << 20) && (2 * N) % bn == 0 && N <= (1 << 20);
+    return aligned && M >= 128 && M < ((int64_t)1 << 31) && K >= 16 && K <= (1 << 20) && N <= (1 << 20) &&
+           large_variant(prec, M, 2 * K, 2 * N, true) != 0;
 }
 
 cudaError_t launch_tc_cgemm_large(const float2 *A, const float2 *B, float2 *C, int64_t M, int64_t K,
                                   int64_t N, tn_precision prec, int *err, cudaStream_t st) {
-    switch (prec) {
-        // measured per precision (M = 65536, K = N = 512): TF32 x3 and BF16 x1
-        // run faster with A split in place in shared memory (0.62 vs 0.59 of
-        // the TF32 peak; 0.42 vs 0.38), BF16 x3 on 256-column tiles in shared
-        // memory (0.59 vs 0.55 on 128-column tiles with A in tensor memory)
-        case TN_PREC_TF32x3: return run_large<1>(A, B, C, M, (int)K, (int)N, err, st);
-        case TN_PREC_BF16x3:
-            return bf16x3_wide_tiles(M, N) ? run_large<2>(A, B, C, M, (int)K, (int)N, err, st)
-                                           : run_tmem<2>(A, B, C, M, (int)K, (int)N, err, st);
-        case TN_PREC_BF16x1: return run_large<3>(A, B, C, M, (int)K, (int)N, err, st);
-        default: return cudaErrorInvalidValue;
-    }
+    LgBSource bs;
+    bs.B = B;
+    return run_any(prec, A, bs, C, M, K, N, err, st);
+}
+
+bool tc_large_stem_supported(int64_t M, int k, int n, tn_precision prec, const void *A, const void *C) {
+    if (prec == TN_PREC_FP32_SIMT) return false;
+    const int64_t K = (int64_t)1 << k, N = (int64_t)1 << n;
+    const bool aligned = !((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(C)) & 15);
+    return aligned && M >= 128 && M < ((int64_t)1 << 31) && K >= 16 && N >= 16 &&
+           large_variant(prec, M, 2 * K, 2 * N, false) != 0;
+}
+
+cudaError_t launch_tc_stem_gemm_large(const float2 *A, float2 *C, int64_t M, int k, int n,
+                                      const DevBranch *d_branch_entry, const float2 *pool, BatchArgs ba,
+                                      tn_precision prec, int *err, cudaStream_t st) {
+    LgBSource bs;
+    bs.br = d_branch_entry;
+    bs.pool = pool;
+    bs.ba = ba;
+    return run_any(prec, A, bs, C, M, (int64_t)1 << k, (int64_t)1 << n, err, st);
 }
 
 }  // namespace tn

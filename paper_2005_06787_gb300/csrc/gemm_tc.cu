@@ -660,6 +660,10 @@ cudaError_t launch_tc_stem_gemm(const float2 *A, float2 *C, int64_t M, int k, in
                                 int64_t strideA, int64_t strideC, const DevBranch *d_branch_entry,
                                 const float2 *pool, BatchArgs ba, tn_precision prec,
                                 cudaStream_t st) {
+    // one batch item and 2^k, 2^n >= 16: the TMA-fed pipelined kernels (the
+    // branch of the item's slice is split on the device first)
+    if (g_tc_err && ba.n_items == 1 && tc_large_stem_supported(M, k, n, prec, A, C))
+        return launch_tc_stem_gemm_large(A, C, M, k, n, d_branch_entry, pool, ba, prec, g_tc_err, st);
     TcArgs a{};
     a.A = reinterpret_cast<const float *>(A);
     a.C = reinterpret_cast<float *>(C);

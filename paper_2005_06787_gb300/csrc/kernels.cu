@@ -849,7 +849,8 @@ cudaError_t launch_stem_gemm(const float2 *A, float2 *C, int64_t M, int k, int n
                              int64_t strideC, const DevBranch *d_branch_entry, const float2 *pool,
                              BatchArgs ba, tn_precision prec, cudaStream_t st) {
     if (prec != TN_PREC_FP32_SIMT) {
-        if (!tc_gemm_supported(k, n)) return cudaErrorNotSupported;
+        if (!tc_gemm_supported(k, n) && !(ba.n_items == 1 && tc_large_stem_supported(M, k, n, prec, A, C)))
+            return cudaErrorNotSupported;
         return launch_tc_stem_gemm(A, C, M, k, n, strideA, strideC, d_branch_entry, pool, ba, prec, st);
     }
     GemmItemSrc g{A, C, nullptr, strideA, 0, strideC, d_branch_entry, pool, ba, 1};

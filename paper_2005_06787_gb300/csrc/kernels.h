@@ -115,6 +115,12 @@ cudaError_t measure_fma_peak(cudaStream_t st, double *tflops, int *sm_count);
 bool tc_large_supported(int64_t M, int64_t K, int64_t N, tn_precision prec, const void *A, const void *C);
 cudaError_t launch_tc_cgemm_large(const float2 *A, const float2 *B, float2 *C, int64_t M, int64_t K,
                                   int64_t N, tn_precision prec, int *err, cudaStream_t st);
+// A stem GEMM step of one batch item (2^k x 2^n branch of the launch's slice)
+// on the same TMA-fed kernels: 2^k, 2^n >= 16, M >= 128.
+bool tc_large_stem_supported(int64_t M, int k, int n, tn_precision prec, const void *A, const void *C);
+cudaError_t launch_tc_stem_gemm_large(const float2 *A, float2 *C, int64_t M, int k, int n,
+                                      const DevBranch *d_branch_entry, const float2 *pool, BatchArgs ba,
+                                      tn_precision prec, int *err, cudaStream_t st);
 
 bool tc_gemm_supported(int k, int n);
 cudaError_t tc_gemm_init();

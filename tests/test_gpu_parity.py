@@ -121,17 +121,20 @@ def test_cgemm_tensor_core_matches_fp64(prec, M, K, N, batch):
     assert rel_l2(got, ref) < TC_TOL[prec], rel_l2(got, ref)
 
 
-# Shapes of the TMA-pipelined tcgen05 kernel (K >= 32 and 2N a multiple of its
-# tile width: 128 for x3, 256 for BF16 x1), including ragged M (partial last
-# tile, rows past M read as zero and not stored), batches (one launch per
-# item) and the large benchmark shape, whose reference is checked on sampled
-# rows (every row must be written: C starts as NaN).
+# Shapes of the TMA-pipelined tcgen05 kernels (K >= 16, 2N a multiple of 32,
+# M >= 128), including ragged M (partial last tile, rows past M read as zero
+# and not stored), batches (one launch per item) and the large benchmark
+# shape, whose reference is checked on sampled rows (every row must be
+# written: C starts as NaN).
 @pytest.mark.parametrize("prec", ["tf32x3", "bf16x3", "bf16x1"])
 # (38000, 64, 512) and (65536, 512, 512) fill enough waves of the GPU that
-# 3xBF16 takes its 256-column kernel (the others take the 128-column one).
+# 3xBF16 takes its 256-column kernel (the others take the 128-column one);
+# N = 16 and 32 take 32- and 64-column tiles, and K = 16 a k-block that the
+# copy pads with zeros past 2K (BF16 stages hold 64 real K).
 @pytest.mark.parametrize("M,K,N,batch", [(128, 32, 128, 1), (1000, 64, 128, 1), (130, 32, 256, 2),
                                          (4096, 256, 64, 1), (2048, 128, 512, 1), (16384, 512, 512, 1),
-                                         (38000, 64, 512, 1), (65536, 512, 512, 1)])
+                                         (38000, 64, 512, 1), (65536, 512, 512, 1), (4096, 16, 16, 1),
+                                         (1000, 32, 16, 1), (3000, 16, 32, 2), (65536, 32, 32, 1)])
 def test_cgemm_large_tensor_core_matches_fp64(prec, M, K, N, batch):
     A = random_complex((batch, M, K), 31, np.complex64)
     B = random_complex((batch, K, N), 32, np.complex64)
