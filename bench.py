@@ -167,6 +167,9 @@ def stored_slices(name: str):
     if not os.path.exists(path):
         return None, None
     g = json.load(open(path))
+    sch_path = os.path.join(GOLDEN, f"{name}_scheme.json")
+    if os.path.exists(sch_path) and json.load(open(sch_path))["sliced_wires"] != g["sliced_wires"]:
+        return None, None  # values of another scheme's slices
     vals = {int(k): np.asarray(v["re"]) + 1j * np.asarray(v["im"]) for k, v in g["slices"].items()}
     secs = {int(k): v.get("seconds") for k, v in g["slices"].items()}
     return vals, {"seconds": secs, "threads": g.get("threads")}
