@@ -418,7 +418,7 @@ def hyperedge_run(stream):
 
 
 def twenty_cycle_run(stream, n_slices: int = 8):
-    """The 20-cycle workload on its best stored plan (total cost 2^62.09, 23
+    """The 20-cycle workload on its best stored plan (total cost 2^61.99, 23
     sliced edges, cw 30; tests/golden/diag53_m20_scheme.json) in the bench's
     launch configuration: seeded slices timed, the whole 64-amplitude batch
     extrapolated (Supp. A.4: per-subtask time x number of subtasks)."""

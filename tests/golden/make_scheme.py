@@ -44,8 +44,9 @@ def main(name: str, extra: dict):
 
 if __name__ == "__main__":
     # optional second argument: planner options beyond bench.plan_options, as
-    # JSON, e.g. the 20-cycle plan of total cost 2^62.09:
-    #   python make_scheme.py diag53_m20 '{"start_cluster": 148, "anneal_iters": 1200000,
+    # JSON, e.g. the stored 20-cycle plan of total cost 2^61.99 (all 386 start
+    # clusters, about an hour on 8 host cores):
+    #   python make_scheme.py diag53_m20 '{"stem_starts": 386, "anneal_iters": 1200000,
     #       "restarts": 1, "slice_restarts": 0, "max_sliced": 64}'
     main(sys.argv[1] if len(sys.argv) > 1 else "diag53_m14",
          json.loads(sys.argv[2]) if len(sys.argv) > 2 else {})

@@ -639,7 +639,7 @@ def test_diag53_m14_merged_gemm_steps_per_precision(prec, capsys):
     assert max(errs) < tol
 
 
-# The 20-cycle workload with its best plan (total cost 2^62.09: cw 30, 23
+# The 20-cycle workload with its best plan (total cost 2^61.99: cw 30, 23
 # sliced edges; tests/golden/diag53_m20_scheme.json, exported by
 # make_scheme.py with the options it records): real gates, the bench's launch
 # configuration. Slice 0 against the stored FP64 oracle value; 8 seeded
